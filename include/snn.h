@@ -1,0 +1,189 @@
+/*
+ * snn.h -- C ABI of the GB300 (sm_103a) simulator of a DPSNN-style cortical grid.
+ *
+ * Model (Pastorelli et al. 2019, Sec. 2.2): a gx x gy grid of modules of
+ * K = 1250 leaky integrate-and-fire neurons with spike-frequency adaptation
+ * (Eq. 2), populations F / B / I = local indices 0..249 / 250..999 / 1000..1249;
+ * neuron id = module * 1250 + local, module = y * gx + x.  Each neuron projects
+ * M (1125 = 0.9 K) synapses; excitatory targets fall off with module distance as
+ * exp(-d/lambda) (Eq. 1), inhibitory targets stay in the source module;
+ * efficacies are Gaussian (mean J, SD dJ_frac*|J|); every neuron also receives a
+ * Poisson drive of N_ext trains at nu_ext with Gaussian amplitudes (Sec. 2.1,
+ * Table S1).  The simulation is time driven with dt = dt_ms, delays of
+ * 1..n_delay steps, and synaptic input accumulated in int32 fixed point of
+ * 2^-16 mV, so spike rasters do not depend on delivery order.
+ *
+ * Conventions:
+ *   - Every call returns 0 (SNN_OK) or a negative SNN_ERR_* code; the message of
+ *     the last failure on the calling thread is available from snn_last_error().
+ *   - The library owns all device memory of a network (allocated through the
+ *     allocator installed with snn_set_allocator, cudaMalloc otherwise) and the
+ *     caller owns every host buffer passed in.  Pointers named *_out are host
+ *     pointers written by the call.
+ *   - There is no CPU fallback: without a usable CUDA device every call that
+ *     needs one returns SNN_ERR_CUDA.
+ *   - A network is not thread safe; distinct networks may be used from
+ *     distinct threads.
+ */
+#ifndef SNN_H
+#define SNN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SNN_OK 0
+#define SNN_ERR_ARG -1       /* invalid argument or parameter set */
+#define SNN_ERR_OOM -2       /* device or host allocation failed */
+#define SNN_ERR_CUDA -3      /* CUDA runtime error or no device */
+#define SNN_ERR_TIMEOUT -4   /* a bounded device wait gave up; results of the call are invalid */
+#define SNN_ERR_BUFFER -5    /* caller buffer too small; *n_out holds the required count */
+#define SNN_ERR_LIMIT -6     /* size beyond an implementation limit (e.g. N >= 2^24 neurons) */
+#define SNN_ERR_STATE -7     /* call not valid in the current state */
+
+#define SNN_REC_F32 0        /* synapse record: u32 (delay << 24 | target) + f32 weight (8 B) */
+#define SNN_REC_I16 1        /* synapse record: u32 (delay << 24 | target) + i16 weight in 2^-10 mV (6 B) */
+
+#define SNN_K 1250           /* neurons per module (Sec. 2.2) */
+
+/* Model parameters.  Arrays indexed [population] use F = 0, B = 1, I = 2. */
+typedef struct snn_params {
+  int32_t gx, gy;          /* grid of modules */
+  float lambda;            /* Eq. 1 decay length, in inter-module distances */
+  float p_local;           /* >= 0: share of excitatory out-degree kept in the source
+                              module, the rest over the other modules ~ exp(-d/lambda);
+                              < 0: pure Eq. 1 kernel over all modules, source included */
+  int32_t out_degree;      /* M, synapses per neuron (1125) */
+  int32_t n_delay;         /* delays uniform on 1..n_delay steps (1..254) */
+  float dt_ms;             /* time step (0.1 ms) */
+  int32_t record_format;   /* SNN_REC_F32 or SNN_REC_I16 */
+  int32_t bin_steps;       /* steps per rate bin (50 = 5 ms, Sec. 2.3) */
+  float tau_m[3];          /* membrane time constant, ms (Table S1) */
+  float C_m[3];            /* capacitance, pF */
+  float E_L[3];            /* resting potential, mV */
+  float V_th[3];           /* threshold, mV; a spike when V > V_th */
+  float V_r[3];            /* reset, mV, held for tau_arp */
+  float tau_arp[3];        /* absolute refractory period, ms */
+  float alpha_c[3];        /* adaptation jump per spike, mV (0 = no adaptation) */
+  float tau_c[3];          /* adaptation time constant, ms */
+  float g_c[3];            /* adaptation conductance, nS (g_c/C_m in 1/ms) */
+  float J[3][3];           /* mean efficacy J[target population][source population], mV */
+  float dJ_frac;           /* efficacy SD as a fraction of |J| (0.25) */
+  float J_ext[3];          /* mean external efficacy, mV */
+  float dJ_ext_frac;       /* external efficacy SD as a fraction of |J_ext| (0.25) */
+  float nu_ext[3];         /* rate per external train, Hz */
+  float N_ext[3];          /* external trains per neuron (400) */
+} snn_params;
+
+typedef struct snn_net *snn_handle;
+
+/* Counters of one network. */
+typedef struct snn_stats {
+  uint64_t t;              /* steps simulated so far */
+  uint64_t spikes;         /* spikes emitted */
+  uint64_t rec_events;     /* recurrent synaptic events delivered (= spikes * M) */
+  uint64_t ext_events;     /* external (Poisson) events drawn */
+  uint64_t n_neurons;
+  uint64_t n_synapses;     /* recurrent synapses stored */
+  uint64_t device_bytes;   /* device memory held by the network */
+  uint64_t record_bytes;   /* of which synapse records */
+  double build_ms;         /* wall time of snn_build_network */
+} snn_stats;
+
+/* Launch shapes; chosen by snn_autotune or set explicitly. */
+typedef struct snn_launch {
+  int32_t path;            /* 0 = two kernels per step (update, deliver); 1 = fused step kernel */
+  int32_t update_block;    /* threads per update block: 128, 256 or 512 */
+  int32_t deliver_warps;   /* warps per deliver block: 1..8 */
+  int32_t fused_block;     /* threads per fused-step block: 128..512 */
+  int32_t fused_items_per_sm; /* resident fused blocks per SM to launch (1..8) */
+  int32_t window_steps;    /* steps per captured CUDA graph (1..4096) */
+  int32_t deliver_chunk;   /* synapse records per delivery work item, multiple of 8
+                              (two-kernel path <= 1152, fused path <= 576) */
+} snn_launch;
+
+typedef void *(*snn_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*snn_free_fn)(void *ptr, void *ctx);
+
+/* Install the device allocator used for all later allocations (e.g. PyTorch's
+ * caching allocator).  NULL functions restore cudaMalloc/cudaFree.  Memory
+ * must be device memory of the current device, 256-byte aligned.  Networks
+ * keep the functions that allocated them. */
+int snn_set_allocator(snn_alloc_fn alloc, snn_free_fn free_fn, void *ctx);
+
+/* Device bytes a network with these parameters will hold once built
+ * (synapse records, neuron state, delay ring, tables, recording buffers). */
+int snn_footprint(const snn_params *p, size_t *bytes_out);
+
+/* Build a network on the device (Sec. 2.1 initialisation; Eq. 1 connectivity,
+ * Sec. 2.2 efficacies).  Synapse j of source neuron s is a pure function of
+ * (seed, s, j) drawn from Philox4x32-10, each outgoing row is stored ordered
+ * by delay (ties in draw order), and the initial V is uniform on [0, V_th).
+ * `cuda_stream` (a cudaStream_t, or NULL for the legacy default stream) is the
+ * stream every later call of this network is ordered on.  The call returns
+ * when the network is ready.  Errors: SNN_ERR_ARG (bad parameters),
+ * SNN_ERR_LIMIT (N >= 2^24 neurons or M > 4096), SNN_ERR_OOM, SNN_ERR_CUDA. */
+int snn_build_network(const snn_params *p, uint64_t seed, void *cuda_stream, snn_handle *out);
+
+/* Advance the network by `steps` time steps (Eq. 2 update with Poisson drive,
+ * spike detection, delivery of each spike's row into the delay ring) and
+ * record spikes and rate counts.  Returns after the steps completed and their
+ * records reached host memory.  Errors: SNN_ERR_TIMEOUT (a bounded wait in a
+ * kernel gave up), SNN_ERR_CUDA. */
+int snn_run(snn_handle h, uint64_t steps);
+
+/* Advance n networks together by steps[i] each with one fused kernel per time
+ * step over all of them (networks that reach their count stop early).  Each
+ * network's results are identical to snn_run on it alone.  The networks must
+ * share one device; the call is ordered on the first network's stream. */
+int snn_run_batch(const snn_handle *hs, const uint64_t *steps, int32_t n);
+
+/* Spikes with t0 <= step < t1, ordered by (step, id), as two parallel host
+ * arrays of capacity `cap`.  *n_out receives the count; if it exceeds cap
+ * nothing is written and SNN_ERR_BUFFER is returned. */
+int snn_read_spikes(snn_handle h, uint64_t t0, uint64_t t1, uint32_t *step_out, uint32_t *id_out,
+                    size_t cap, size_t *n_out);
+
+/* Spike counts per (bin, module, population) for all completed steps, layout
+ * [bin][module][F, B, I], bin = step / bin_steps (Sec. 2.3 rates; Hz =
+ * count / (population size * bin_steps * dt)).  *n_out = bins * G * 3. */
+int snn_rates(snn_handle h, uint32_t *counts_out, size_t cap, size_t *n_out);
+
+/* Copy the neuron state (V in mV, c in mV, remaining refractory steps) of all
+ * N neurons to host arrays of length n >= N. */
+int snn_read_state(snn_handle h, float *V_out, float *c_out, int32_t *ref_out, size_t n);
+
+/* Copy the stored outgoing row of source neuron s: M record keys
+ * (delay << 24 | target) and weights in mV (for SNN_REC_I16, q * 2^-10). */
+int snn_read_row(snn_handle h, uint32_t s, uint32_t *keys_out, float *w_out, size_t cap);
+
+int snn_get_stats(snn_handle h, snn_stats *out);
+
+/* Launch shapes (results never depend on them). */
+int snn_get_launch(snn_handle h, snn_launch *out);
+int snn_set_launch(snn_handle h, const snn_launch *cfg);
+
+/* Time candidate launch shapes on this network for `trial_steps` steps each
+ * and keep the fastest; the network's state, counters and records are
+ * restored afterwards, so results are unchanged. */
+int snn_autotune(snn_handle h, uint32_t trial_steps);
+
+/* Release the network and its device memory. */
+void snn_free(snn_handle h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *snn_last_error(void);
+
+/* Testing aid: iteration limit of the kernels' bounded waits on their own
+ * asynchronous copies (default about one second).  With 0 every wait gives up
+ * at once: the kernel records SNN_ERR_TIMEOUT, waits with the default limit
+ * for its copies in flight, and returns; the network is then invalid. */
+int snn_debug_set_wait_limit(snn_handle h, uint32_t iterations);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SNN_H */

@@ -1,0 +1,980 @@
+// snn_host.cpp -- host runtime of the C ABI declared in include/snn.h.
+//
+// Responsibilities: validate parameters, build the small FP64 tables the
+// kernels consume (Eq. 2 propagators, Poisson thresholds, Gaussian quantiles,
+// Eq. 1 module thresholds), own each network's device arena, capture windows
+// of time steps into CUDA graphs, and drain spike records and rate counts to
+// host memory after every window.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/snn.h"
+#include "snn_internal.h"
+
+using namespace snn;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+static int fail(int code, const std::string &msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define CU_TRY(expr)                                                                          \
+  do {                                                                                        \
+    cudaError_t _e = (expr);                                                                  \
+    if (_e != cudaSuccess) return fail(SNN_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+extern "C" const char *snn_last_error(void) { return g_last_error.c_str(); }
+
+// ---------------------------------------------------------------------------
+// allocator
+// ---------------------------------------------------------------------------
+struct AllocFns {
+  snn_alloc_fn alloc = nullptr;
+  snn_free_fn free_fn = nullptr;
+  void *ctx = nullptr;
+};
+static std::mutex g_alloc_mu;
+static AllocFns g_alloc;
+
+extern "C" int snn_set_allocator(snn_alloc_fn alloc, snn_free_fn free_fn, void *ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return fail(SNN_ERR_ARG, "alloc and free must both be set or both be NULL");
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc.alloc = alloc;
+  g_alloc.free_fn = free_fn;
+  g_alloc.ctx = ctx;
+  return SNN_OK;
+}
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  AllocFns fns;
+  void release() {
+    if (!p) return;
+    if (fns.free_fn) fns.free_fn(p, fns.ctx);
+    else cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+};
+
+static int dev_alloc(DevBuf &b, size_t bytes) {
+  AllocFns fns;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    fns = g_alloc;
+  }
+  void *p = nullptr;
+  if (fns.alloc) {
+    p = fns.alloc(bytes, fns.ctx);
+    if (!p) return fail(SNN_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+  } else {
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(e == cudaErrorMemoryAllocation ? SNN_ERR_OOM : SNN_ERR_CUDA,
+                  "cudaMalloc(" + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    }
+  }
+  if (reinterpret_cast<uintptr_t>(p) % 256 != 0) {
+    if (fns.free_fn) fns.free_fn(p, fns.ctx); else cudaFree(p);
+    return fail(SNN_ERR_ARG, "allocator returned memory that is not 256-byte aligned");
+  }
+  b.p = p;
+  b.bytes = bytes;
+  b.fns = fns;
+  return SNN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// host tables (FP64, rounded once)
+// ---------------------------------------------------------------------------
+namespace {
+
+double std_normal_cdf(double x) { return 0.5 * std::erfc(-x / std::sqrt(2.0)); }
+
+// Inverse of the standard normal CDF: a coarse bracket by halving, then
+// Newton steps on Phi(x) - p until the correction vanishes.
+double inverse_normal_cdf(double p) {
+  double a = -12.0, b = 12.0;
+  for (int i = 0; i < 48; ++i) {
+    const double c = 0.5 * (a + b);
+    if (std_normal_cdf(c) < p) a = c; else b = c;
+  }
+  double x = 0.5 * (a + b);
+  const double inv_sqrt_2pi = 0.3989422804014327;
+  for (int i = 0; i < 8; ++i) {
+    const double dens = inv_sqrt_2pi * std::exp(-0.5 * x * x);
+    const double step = (std_normal_cdf(x) - p) / dens;
+    const double xn = x - step;
+    if (xn == x) break;
+    x = xn;
+  }
+  // settle on the smallest double with Phi(x) >= p
+  for (int i = 0; i < 256 && std_normal_cdf(x) < p; ++i) x = std::nextafter(x, 1e300);
+  for (int i = 0; i < 256; ++i) {
+    const double dn = std::nextafter(x, -1e300);
+    if (std_normal_cdf(dn) >= p) x = dn; else break;
+  }
+  return x;
+}
+
+struct PopTables {
+  float pvv, pvc, pcc;
+  int32_t narp;
+  unsigned long long thr[kPoisMax];
+};
+
+PopTables pop_tables(const snn_params &p, int q) {
+  PopTables t{};
+  const double dt = (double)p.dt_ms, tm = (double)p.tau_m[q], tc = (double)p.tau_c[q];
+  const double g_over_c = (double)p.g_c[q] / (double)p.C_m[q];
+  const double decay_m = std::exp(-dt / tm);
+  const double decay_c = std::exp(-dt / tc);
+  // V(dt) picks up -(g/C) * int_0^dt exp(-(dt-s)/tau_m) c(0) exp(-s/tau_c) ds
+  double coupling;
+  if (tc == tm) coupling = -(g_over_c * dt) * decay_m;
+  else coupling = -(g_over_c * (tm * tc / (tc - tm))) * (decay_c - decay_m);
+  t.pvv = (float)decay_m;
+  t.pcc = (float)decay_c;
+  t.pvc = (float)coupling;
+  t.narp = (int32_t)std::lround((double)p.tau_arp[q] / dt);
+  const double lam = (double)p.N_ext[q] * (double)p.nu_ext[q] * (double)p.dt_ms / 1000.0;
+  double pk = std::exp(-lam), acc = pk;
+  for (int k = 0; k < kPoisMax; ++k) {
+    if (k) {
+      pk = (pk * lam) / (double)k;
+      acc = acc + pk;
+    }
+    t.thr[k] = (unsigned long long)std::floor(acc * 4294967296.0);
+  }
+  return t;
+}
+
+float sign_kept(float w, float mean) {
+  if (mean > 0.0f && w < 0.0f) return 0.0f;
+  if (mean < 0.0f && w > 0.0f) return 0.0f;
+  return w;
+}
+
+// Thresholds T[0..G-2] of the target-module distribution of every source
+// module (Eq. 1), built from one table of kernel values per displacement.
+void module_thresholds(const snn_params &p, std::vector<uint32_t> &out) {
+  const int gx = p.gx, gy = p.gy, G = gx * gy;
+  out.assign((size_t)G * (size_t)(G - 1), 0u);
+  if (G < 2) return;
+  const double lam = (double)p.lambda, pl = (double)p.p_local;
+  std::vector<double> kern((size_t)gx * gy);   // kernel value for |dx|, |dy|
+  for (int ay = 0; ay < gy; ++ay)
+    for (int ax = 0; ax < gx; ++ax) {
+      const double dx = (double)ax, dy = (double)ay;
+      kern[(size_t)ay * gx + ax] = std::exp(-(std::sqrt(dx * dx + dy * dy) / lam));
+    }
+  auto kv = [&](int m, int src) {
+    const int ax = std::abs(m % gx - src % gx), ay = std::abs(m / gx - src / gx);
+    return kern[(size_t)ay * gx + ax];
+  };
+  for (int src = 0; src < G; ++src) {
+    double total = 0.0;
+    for (int m = 0; m < G; ++m) {
+      if (pl >= 0.0 && m == src) continue;
+      total = total + kv(m, src);
+    }
+    double acc = 0.0;
+    uint32_t *T = out.data() + (size_t)src * (size_t)(G - 1);
+    for (int m = 0; m + 1 < G; ++m) {
+      double pm;
+      if (pl >= 0.0) pm = (m == src) ? pl : ((1.0 - pl) * kv(m, src)) / total;
+      else pm = kv(m, src) / total;
+      acc = acc + pm;
+      const double f = std::floor(acc * 4294967296.0);
+      T[m] = f >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)f;
+    }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// network object
+// ---------------------------------------------------------------------------
+// Device arena of one network, in this order: V, c, ref, ring (the state a run
+// modifies), synapse rows, amplitude table, window, recording block (header,
+// external-event slots, rate window: one contiguous copy per window), raster
+// entries.
+struct Layout {
+  size_t off_V, off_c, off_ref, off_ring, off_rows, off_amp, off_win;
+  size_t off_rec, off_ext, off_rates, off_entries, total;
+  uint32_t N, N_pad, G, M, M_pad, D, row_bytes;
+  uint32_t window, rates_bins, rec_cap, n_ext_slots;
+};
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+static int validate(const snn_params &p) {
+  if (p.gx < 1 || p.gy < 1) return fail(SNN_ERR_ARG, "grid must be at least 1x1");
+  if (!(p.lambda > 0.0f) || !std::isfinite(p.lambda)) return fail(SNN_ERR_ARG, "lambda must be > 0");
+  if (!std::isfinite(p.p_local) || p.p_local > 1.0f) return fail(SNN_ERR_ARG, "p_local must be <= 1");
+  if (p.out_degree < 1) return fail(SNN_ERR_ARG, "out_degree must be >= 1");
+  if (p.out_degree > 2048) return fail(SNN_ERR_LIMIT, "out_degree above 2048");
+  if (p.n_delay < 1 || p.n_delay > 254) return fail(SNN_ERR_ARG, "n_delay must be in 1..254");
+  if (!(p.dt_ms > 0.0f)) return fail(SNN_ERR_ARG, "dt_ms must be > 0");
+  if (p.record_format != SNN_REC_F32 && p.record_format != SNN_REC_I16) return fail(SNN_ERR_ARG, "unknown record_format");
+  if (p.bin_steps < 1) return fail(SNN_ERR_ARG, "bin_steps must be >= 1");
+  for (int q = 0; q < 3; ++q) {
+    if (!(p.tau_m[q] > 0.0f) || !(p.tau_c[q] > 0.0f) || !(p.C_m[q] > 0.0f))
+      return fail(SNN_ERR_ARG, "tau_m, tau_c, C_m must be > 0");
+    if (p.tau_arp[q] < 0.0f || p.N_ext[q] < 0.0f || p.nu_ext[q] < 0.0f)
+      return fail(SNN_ERR_ARG, "tau_arp, N_ext, nu_ext must be >= 0");
+    const double narp = std::lround((double)p.tau_arp[q] / (double)p.dt_ms);
+    if (narp > 255) return fail(SNN_ERR_LIMIT, "refractory period above 255 steps");
+  }
+  const uint64_t N = (uint64_t)p.gx * (uint64_t)p.gy * (uint64_t)kK;
+  if (N >= (1ull << 24)) return fail(SNN_ERR_LIMIT, "N >= 2^24 neurons (24-bit target index)");
+  return SNN_OK;
+}
+
+static Layout make_layout(const snn_params &p) {
+  Layout L{};
+  L.G = (uint32_t)(p.gx * p.gy);
+  L.N = L.G * (uint32_t)kK;
+  L.N_pad = (uint32_t)align_up(L.N, kNeuronAlign);
+  L.M = (uint32_t)p.out_degree;
+  L.M_pad = (uint32_t)align_up(L.M, 8);
+  L.D = (uint32_t)p.n_delay + 1u;
+  L.row_bytes = L.M_pad * 4u + L.M_pad * (p.record_format == SNN_REC_I16 ? 2u : 4u);
+  L.n_ext_slots = L.N_pad / 128u;
+  int narp_min = 255;
+  for (int q = 0; q < 3; ++q)
+    narp_min = std::min(narp_min, (int)std::lround((double)p.tau_arp[q] / (double)p.dt_ms));
+  // A neuron fires at most once per narp_min + 1 steps, so a window of W steps
+  // holds at most N * ceil(W / (narp_min + 1)) raster entries: size the window
+  // so that this bound fits the entry budget, and the raster can never overflow.
+  const size_t budget = 192ull << 20;
+  const size_t per_step = (size_t)L.N * 8u / (size_t)(narp_min + 1) + 8u;
+  L.window = (uint32_t)std::max<size_t>(16, std::min<size_t>(1024, budget / per_step));
+  L.rec_cap = (uint32_t)std::min<uint64_t>(0xFFFFFFF0ull,
+                                           (uint64_t)L.N * ((L.window + narp_min) / (narp_min + 1) + 1));
+  L.rates_bins = L.window / (uint32_t)p.bin_steps + 2u;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align_up(o + bytes, 256);
+    return at;
+  };
+  L.off_V = take((size_t)L.N_pad * 4);
+  L.off_c = take((size_t)L.N_pad * 4);
+  L.off_ref = take((size_t)L.N_pad);
+  L.off_ring = take((size_t)L.D * L.N_pad * 4);
+  L.off_rows = take((size_t)L.N * L.row_bytes);
+  L.off_amp = take((size_t)kNPop * kZTab * 4);
+  L.off_win = take(sizeof(NetWin));
+  L.off_rec = o;
+  L.off_ext = L.off_rec + 256;
+  L.off_rates = align_up(L.off_ext + (size_t)L.n_ext_slots * 8, 256);
+  o = align_up(L.off_rates + (size_t)L.rates_bins * L.G * 3 * 4, 256);
+  L.off_entries = take((size_t)L.rec_cap * 8);
+  L.total = o;
+  return L;
+}
+
+struct snn_net {
+  snn_params p{};
+  uint64_t seed = 0;
+  cudaStream_t stream = nullptr;     // caller's stream
+  cudaStream_t cap_stream = nullptr; // private stream used for graph capture
+  DevBuf arena;
+  Layout L{};
+  NetDev hd{};                       // static descriptor (kernel parameter)
+  NetWin *pinned_win = nullptr;      // pinned staging of the window
+  uint8_t *pinned_rec = nullptr;     // pinned copy of the recording block
+  unsigned long long *pinned_entries = nullptr;
+  size_t pinned_entries_cap = 0;
+  snn_launch cfg{};
+  cudaGraphExec_t exec = nullptr;
+  uint32_t exec_window = 0;
+  snn_launch exec_cfg{};
+  uint32_t exec_wait_limit = 0;
+  uint32_t wait_limit = 1u << 22;
+  // host records
+  uint64_t t = 0;
+  std::vector<unsigned long long> raster;   // (step << 32 | id), non-decreasing in step
+  size_t raster_sorted = 0;
+  std::vector<uint32_t> rates;              // [bin][G][3]
+  uint64_t spikes = 0, ext_events = 0;
+  double build_ms = 0.0;
+  bool broken = false;
+  int sm_count = 0;
+};
+
+static int sm_count_cached() {
+  static int v = 0;
+  if (!v) v = device_sm_count();
+  return v;
+}
+
+static void default_launch(snn_net *h) {
+  h->cfg.path = 0;
+  h->cfg.update_block = 256;
+  h->cfg.deliver_warps = 4;
+  h->cfg.fused_block = 256;
+  h->cfg.fused_items_per_sm = 2;
+  h->cfg.window_steps = (int32_t)h->L.window;
+  h->cfg.deliver_chunk = 384;
+}
+
+extern "C" int snn_footprint(const snn_params *p, size_t *bytes_out) {
+  if (!p || !bytes_out) return fail(SNN_ERR_ARG, "null argument");
+  int rc = validate(*p);
+  if (rc) return rc;
+  *bytes_out = make_layout(*p).total;
+  return SNN_OK;
+}
+
+static void free_net(snn_net *h) {
+  if (!h) return;
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->pinned_win) cudaFreeHost(h->pinned_win);
+  if (h->pinned_rec) cudaFreeHost(h->pinned_rec);
+  if (h->pinned_entries) cudaFreeHost(h->pinned_entries);
+  h->arena.release();
+  delete h;
+}
+
+extern "C" void snn_free(snn_handle h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  free_net(h);
+}
+
+static void fill_descriptor(snn_net *h) {
+  const Layout &L = h->L;
+  uint8_t *base = static_cast<uint8_t *>(h->arena.p);
+  NetDev &d = h->hd;
+  std::memset(&d, 0, sizeof(d));
+  d.N = L.N;
+  d.N_pad = L.N_pad;
+  d.G = L.G;
+  d.gx = (uint32_t)h->p.gx;
+  d.M = L.M;
+  d.M_pad = L.M_pad;
+  d.D = L.D;
+  d.fmt = (uint32_t)h->p.record_format;
+  d.row_bytes = L.row_bytes;
+  d.bin_steps = (uint32_t)h->p.bin_steps;
+  d.key0 = (uint32_t)(h->seed & 0xFFFFFFFFu);
+  d.key1 = (uint32_t)(h->seed >> 32);
+  d.slot = 0;
+  d.rec_cap = L.rec_cap;
+  d.rates_bins = L.rates_bins;
+  d.wait_limit = h->wait_limit;
+  for (int q = 0; q < 3; ++q) {
+    const PopTables t = pop_tables(h->p, q);
+    d.pvv[q] = t.pvv;
+    d.pvc[q] = t.pvc;
+    d.pcc[q] = t.pcc;
+    d.el[q] = h->p.E_L[q];
+    d.vth[q] = h->p.V_th[q];
+    d.vr[q] = h->p.V_r[q];
+    d.alpha[q] = h->p.alpha_c[q];
+    d.narp[q] = t.narp;
+    for (int k = 0; k < kPoisMax; ++k) d.thr[q][k] = t.thr[k];
+  }
+  d.V = reinterpret_cast<float *>(base + L.off_V);
+  d.c = reinterpret_cast<float *>(base + L.off_c);
+  d.ref = base + L.off_ref;
+  d.ring = reinterpret_cast<int32_t *>(base + L.off_ring);
+  d.rows = base + L.off_rows;
+  d.amp = reinterpret_cast<const int32_t *>(base + L.off_amp);
+  d.win = reinterpret_cast<const NetWin *>(base + L.off_win);
+  d.rec = reinterpret_cast<RecHeader *>(base + L.off_rec);
+  d.ext_acc = reinterpret_cast<unsigned long long *>(base + L.off_ext);
+  d.rates = reinterpret_cast<uint32_t *>(base + L.off_rates);
+  d.rec_entries = reinterpret_cast<unsigned long long *>(base + L.off_entries);
+}
+
+extern "C" int snn_build_network(const snn_params *p, uint64_t seed, void *cuda_stream, snn_handle *out) {
+  if (!p || !out) return fail(SNN_ERR_ARG, "null argument");
+  *out = nullptr;
+  int rc = validate(*p);
+  if (rc) return rc;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(SNN_ERR_CUDA, "no CUDA device available");
+  }
+  const auto t_start = std::chrono::steady_clock::now();
+  std::unique_ptr<snn_net, void (*)(snn_net *)> h(new snn_net(), free_net);
+  h->p = *p;
+  h->seed = seed;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  h->L = make_layout(*p);
+  h->sm_count = sm_count_cached();
+  CU_TRY(prepare_kernels());
+  CU_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  rc = dev_alloc(h->arena, h->L.total);
+  if (rc) return rc;
+  fill_descriptor(h.get());
+  default_launch(h.get());
+  const Layout &L = h->L;
+  cudaStream_t s = h->stream;
+  uint8_t *base = static_cast<uint8_t *>(h->arena.p);
+
+  // tables for construction and the external drive
+  std::vector<float> ztab(kZTab);
+  for (int i = 0; i < kZTab; ++i) ztab[i] = (float)inverse_normal_cdf(((double)i + 0.5) / (double)kZTab);
+  std::vector<int32_t> amp((size_t)kNPop * kZTab);
+  for (int q = 0; q < 3; ++q) {
+    const float sig = p->dJ_ext_frac * std::fabs(p->J_ext[q]);
+    for (int i = 0; i < kZTab; ++i) {
+      const float spread = sig * ztab[i];
+      const float w = sign_kept(p->J_ext[q] + spread, p->J_ext[q]);
+      amp[(size_t)q * kZTab + i] = (int32_t)std::lrintf(w * 65536.0f);
+    }
+  }
+  std::vector<uint32_t> cdf;
+  module_thresholds(*p, cdf);
+  BuildDev bd{};
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      bd.J[a][b] = p->J[a][b];
+      bd.sig[a][b] = p->dJ_frac * std::fabs(p->J[a][b]);
+    }
+  bd.n_delay = (uint32_t)p->n_delay;
+  bd.p_local_mode = p->p_local >= 0.0f ? 1 : 0;
+  DevBuf tmp;
+  const size_t cdf_bytes = std::max<size_t>(cdf.size() * 4, 16);
+  rc = dev_alloc(tmp, align_up(cdf_bytes, 256) + kZTab * 4);
+  if (rc) return rc;
+  struct TmpGuard {
+    DevBuf *b;
+    cudaStream_t s;
+    ~TmpGuard() {
+      cudaStreamSynchronize(s);
+      b->release();
+    }
+  } guard{&tmp, s};
+  uint32_t *d_cdf = static_cast<uint32_t *>(tmp.p);
+  float *d_z = reinterpret_cast<float *>(static_cast<uint8_t *>(tmp.p) + align_up(cdf_bytes, 256));
+  if (!cdf.empty()) CU_TRY(cudaMemcpyAsync(d_cdf, cdf.data(), cdf.size() * 4, cudaMemcpyHostToDevice, s));
+  CU_TRY(cudaMemcpyAsync(d_z, ztab.data(), kZTab * 4, cudaMemcpyHostToDevice, s));
+  CU_TRY(cudaMemcpyAsync(base + L.off_amp, amp.data(), amp.size() * 4, cudaMemcpyHostToDevice, s));
+  bd.cdf = d_cdf;
+  bd.ztab = d_z;
+  CU_TRY(cudaMemsetAsync(base + L.off_ring, 0, (size_t)L.D * L.N_pad * 4, s));
+  CU_TRY(cudaMemsetAsync(base + L.off_win, 0, L.off_entries - L.off_win, s));
+  CU_TRY(cudaMallocHost(&h->pinned_win, sizeof(NetWin)));
+  std::memset(h->pinned_win, 0, sizeof(NetWin));
+  CU_TRY(launch_build_rows(h->hd, bd, s));
+  CU_TRY(launch_init_state(h->hd, s));
+  CU_TRY(cudaMallocHost(&h->pinned_rec, L.off_entries - L.off_rec));
+  CU_TRY(cudaStreamSynchronize(s));
+  h->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  *out = h.release();
+  return SNN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// windows of steps
+// ---------------------------------------------------------------------------
+static int capture_window(snn_net *h, uint32_t window) {
+  if (h->exec && h->exec_window == window && h->exec_wait_limit == h->wait_limit &&
+      std::memcmp(&h->exec_cfg, &h->cfg, sizeof(snn_launch)) == 0)
+    return SNN_OK;
+  if (h->exec) {
+    cudaGraphExecDestroy(h->exec);
+    h->exec = nullptr;
+  }
+  h->hd.wait_limit = h->wait_limit;
+  const snn_launch &c = h->cfg;
+  cudaStream_t cs = h->cap_stream;
+  CU_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  cudaError_t err = cudaSuccess;
+  const int sms = h->sm_count > 0 ? h->sm_count : 148;
+  for (uint32_t k = 0; k < window && err == cudaSuccess; ++k) {
+    err = launch_update(h->hd, k, c.update_block, cs);
+    if (err == cudaSuccess) err = launch_deliver(h->hd, k, (uint32_t)c.deliver_chunk, c.deliver_warps, sms * 4, cs);
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+  if (err != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(SNN_ERR_CUDA, std::string("kernel launch during capture: ") + cudaGetErrorString(err));
+  }
+  if (e2 != cudaSuccess) return fail(SNN_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e2));
+  cudaError_t e3 = cudaGraphInstantiate(&h->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e3 != cudaSuccess) return fail(SNN_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e3));
+  h->exec_window = window;
+  h->exec_cfg = h->cfg;
+  h->exec_wait_limit = h->wait_limit;
+  return SNN_OK;
+}
+
+// Copy a finished window's records to host memory and reset them on the device.
+static int drain_window(snn_net *h, uint64_t t0, cudaStream_t s) {
+  const Layout &L = h->L;
+  uint8_t *base = static_cast<uint8_t *>(h->arena.p);
+  const size_t rec_bytes = L.off_entries - L.off_rec;
+  CU_TRY(cudaMemcpyAsync(h->pinned_rec, base + L.off_rec, rec_bytes, cudaMemcpyDeviceToHost, s));
+  CU_TRY(cudaStreamSynchronize(s));
+  const RecHeader *rh = reinterpret_cast<const RecHeader *>(h->pinned_rec);
+  if (rh->status & kStatusTimeout) {
+    h->broken = true;
+    return fail(SNN_ERR_TIMEOUT, "a bounded wait on an asynchronous copy gave up; the network is invalid");
+  }
+  if (rh->status & kStatusRasterOverflow) {
+    h->broken = true;
+    return fail(SNN_ERR_LIMIT, "spike record window overflowed");
+  }
+  const uint32_t n_rec = std::min(rh->cursor, L.rec_cap);
+  h->spikes += n_rec;
+  const unsigned long long *ext = reinterpret_cast<const unsigned long long *>(h->pinned_rec + (L.off_ext - L.off_rec));
+  for (uint32_t i = 0; i < L.n_ext_slots; ++i) h->ext_events += ext[i];
+  if (n_rec) {
+    if (h->pinned_entries_cap < n_rec) {
+      if (h->pinned_entries) cudaFreeHost(h->pinned_entries);
+      h->pinned_entries = nullptr;
+      size_t cap = std::max<size_t>(n_rec, h->pinned_entries_cap * 2);
+      cap = std::min<size_t>(cap, L.rec_cap);
+      CU_TRY(cudaMallocHost(&h->pinned_entries, cap * 8));
+      h->pinned_entries_cap = cap;
+    }
+    CU_TRY(cudaMemcpyAsync(h->pinned_entries, base + L.off_entries, (size_t)n_rec * 8, cudaMemcpyDeviceToHost, s));
+    CU_TRY(cudaStreamSynchronize(s));
+    const size_t old = h->raster.size();
+    h->raster.resize(old + n_rec);
+    for (uint32_t i = 0; i < n_rec; ++i) {
+      const unsigned long long e = h->pinned_entries[i];
+      const uint64_t k = (e >> 32) & 0xFFFFu;
+      h->raster[old + i] = ((t0 + k) << 32) | (e & 0xFFFFFFFFull);
+    }
+  }
+  // rates of the window, bins from t0 / bin_steps
+  const uint32_t *rw = reinterpret_cast<const uint32_t *>(h->pinned_rec + (L.off_rates - L.off_rec));
+  const uint64_t bin0 = t0 / (uint64_t)h->p.bin_steps;
+  const size_t per_bin = (size_t)L.G * 3;
+  const size_t need = (size_t)(bin0 + L.rates_bins) * per_bin;
+  if (h->rates.size() < need) h->rates.resize(need, 0u);
+  for (size_t i = 0; i < (size_t)L.rates_bins * per_bin; ++i) h->rates[bin0 * per_bin + i] += rw[i];
+  CU_TRY(cudaMemsetAsync(base + L.off_rec, 0, rec_bytes, s));
+  return SNN_OK;
+}
+
+static int run_plain(snn_net *h, uint64_t steps) {
+  const uint32_t window = (uint32_t)std::max(1, std::min<int32_t>(h->cfg.window_steps, (int32_t)h->L.window));
+  int rc = capture_window(h, window);
+  if (rc) return rc;
+  uint8_t *base = static_cast<uint8_t *>(h->arena.p);
+  uint64_t done = 0;
+  while (done < steps) {
+    const uint64_t t0 = h->t;
+    const uint64_t n = std::min<uint64_t>(window, steps - done);
+    if (t0 + n > 0xFFFFFFFFull) return fail(SNN_ERR_LIMIT, "step counter beyond 2^32");
+    h->pinned_win->t0 = (uint32_t)t0;
+    h->pinned_win->t_end = (uint32_t)(t0 + n);
+    h->pinned_win->bin0 = (uint32_t)(t0 / (uint64_t)h->p.bin_steps);
+    CU_TRY(cudaMemcpyAsync(base + h->L.off_win, h->pinned_win, sizeof(NetWin), cudaMemcpyHostToDevice, h->stream));
+    CU_TRY(cudaGraphLaunch(h->exec, h->stream));
+    rc = drain_window(h, t0, h->stream);
+    if (rc) return rc;
+    h->t = t0 + n;
+    done += n;
+  }
+  return SNN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// fused path over a set of networks
+// ---------------------------------------------------------------------------
+struct BatchCtx {
+  DevBuf nets;                 // NetDev[cap]
+  DevBuf wins;                 // NetWin[cap]
+  DevBuf items;                // FusedItem[item_cap]
+  size_t cap = 0, item_cap = 0;
+  NetDev *pinned_nets = nullptr;
+  NetWin *pinned_wins = nullptr;
+  FusedItem *pinned_items = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint32_t exec_window = 0, exec_items = 0, exec_chunk = 0;
+  int exec_block = 0, exec_blocks = 0;
+  ~BatchCtx() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (pinned_nets) cudaFreeHost(pinned_nets);
+    if (pinned_wins) cudaFreeHost(pinned_wins);
+    if (pinned_items) cudaFreeHost(pinned_items);
+    nets.release();
+    wins.release();
+    items.release();
+  }
+};
+static thread_local std::unique_ptr<BatchCtx> g_batch;
+
+static int run_fused(snn_net *const *hs, const uint64_t *steps, int32_t n) {
+  if (!g_batch) g_batch.reset(new BatchCtx());
+  BatchCtx &B = *g_batch;
+  const snn_launch &cfg = hs[0]->cfg;
+  const int block = cfg.fused_block;
+  const uint32_t npi = 4u * (uint32_t)block;
+  const uint32_t chunk = std::min<uint32_t>((uint32_t)cfg.deliver_chunk, max_fused_chunk_records());
+  size_t n_items = 0;
+  uint32_t window = 0xFFFFFFFFu;
+  for (int i = 0; i < n; ++i) {
+    n_items += (hs[i]->L.N_pad + npi - 1) / npi;
+    window = std::min<uint32_t>(window, hs[i]->L.window);
+  }
+  window = std::max<uint32_t>(1, std::min<uint32_t>(window, (uint32_t)std::max(1, cfg.window_steps)));
+  if ((size_t)n > B.cap) {
+    B.nets.release();
+    B.wins.release();
+    if (B.pinned_nets) cudaFreeHost(B.pinned_nets);
+    if (B.pinned_wins) cudaFreeHost(B.pinned_wins);
+    B.pinned_nets = nullptr;
+    B.pinned_wins = nullptr;
+    const size_t cap = std::max<size_t>((size_t)n, 2 * B.cap);
+    int rc = dev_alloc(B.nets, cap * sizeof(NetDev));
+    if (rc) return rc;
+    rc = dev_alloc(B.wins, cap * sizeof(NetWin));
+    if (rc) return rc;
+    CU_TRY(cudaMallocHost(&B.pinned_nets, cap * sizeof(NetDev)));
+    CU_TRY(cudaMallocHost(&B.pinned_wins, cap * sizeof(NetWin)));
+    B.cap = cap;
+    if (B.exec) { cudaGraphExecDestroy(B.exec); B.exec = nullptr; }
+  }
+  if (n_items > B.item_cap) {
+    B.items.release();
+    if (B.pinned_items) cudaFreeHost(B.pinned_items);
+    B.pinned_items = nullptr;
+    const size_t cap = std::max<size_t>(n_items, 2 * B.item_cap);
+    int rc = dev_alloc(B.items, cap * sizeof(FusedItem));
+    if (rc) return rc;
+    CU_TRY(cudaMallocHost(&B.pinned_items, cap * sizeof(FusedItem)));
+    B.item_cap = cap;
+    if (B.exec) { cudaGraphExecDestroy(B.exec); B.exec = nullptr; }
+  }
+  if (!B.cap_stream) CU_TRY(cudaStreamCreateWithFlags(&B.cap_stream, cudaStreamNonBlocking));
+  cudaStream_t s = hs[0]->stream;
+  // all networks of the batch are ordered on the first network's stream
+  for (int i = 0; i < n; ++i)
+    if (hs[i]->stream != s) CU_TRY(cudaStreamSynchronize(hs[i]->stream));
+  size_t it = 0;
+  for (int i = 0; i < n; ++i)
+    for (uint32_t b = 0; b < hs[i]->L.N_pad; b += npi) B.pinned_items[it++] = FusedItem{(uint32_t)i, b};
+  for (int i = 0; i < n; ++i) {
+    NetDev d = hs[i]->hd;
+    d.slot = (uint32_t)i;
+    d.wait_limit = hs[i]->wait_limit;
+    d.win = static_cast<const NetWin *>(B.wins.p) + i;
+    B.pinned_nets[i] = d;
+  }
+  const int sms = hs[0]->sm_count > 0 ? hs[0]->sm_count : 148;
+  const int blocks = (int)std::max<size_t>(1, std::min<size_t>(n_items, (size_t)sms * cfg.fused_items_per_sm));
+  if (!B.exec || B.exec_window != window || B.exec_items != (uint32_t)n_items || B.exec_block != block ||
+      B.exec_blocks != blocks || B.exec_chunk != chunk) {
+    if (B.exec) { cudaGraphExecDestroy(B.exec); B.exec = nullptr; }
+    FusedTable tab{static_cast<const NetDev *>(B.nets.p), static_cast<const FusedItem *>(B.items.p),
+                   (uint32_t)n_items, chunk};
+    CU_TRY(cudaStreamBeginCapture(B.cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = cudaSuccess;
+    for (uint32_t k = 0; k < window && err == cudaSuccess; ++k) err = launch_fused(tab, k, block, blocks, B.cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(B.cap_stream, &g);
+    if (err != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return fail(SNN_ERR_CUDA, std::string("fused launch during capture: ") + cudaGetErrorString(err));
+    }
+    if (e2 != cudaSuccess) return fail(SNN_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e2));
+    cudaError_t e3 = cudaGraphInstantiate(&B.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess) return fail(SNN_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e3));
+    B.exec_window = window;
+    B.exec_items = (uint32_t)n_items;
+    B.exec_block = block;
+    B.exec_blocks = blocks;
+    B.exec_chunk = chunk;
+  }
+  CU_TRY(cudaMemcpyAsync(B.items.p, B.pinned_items, n_items * sizeof(FusedItem), cudaMemcpyHostToDevice, s));
+  CU_TRY(cudaMemcpyAsync(B.nets.p, B.pinned_nets, (size_t)n * sizeof(NetDev), cudaMemcpyHostToDevice, s));
+  std::vector<uint64_t> left(steps, steps + n);
+  while (true) {
+    uint64_t most = 0;
+    for (int i = 0; i < n; ++i) most = std::max(most, left[i]);
+    if (most == 0) break;
+    for (int i = 0; i < n; ++i) {
+      snn_net *h = hs[i];
+      const uint64_t adv = std::min<uint64_t>(window, left[i]);
+      if (h->t + adv > 0xFFFFFFFFull) return fail(SNN_ERR_LIMIT, "step counter beyond 2^32");
+      B.pinned_wins[i].t0 = (uint32_t)h->t;
+      B.pinned_wins[i].t_end = (uint32_t)(h->t + adv);
+      B.pinned_wins[i].bin0 = (uint32_t)(h->t / (uint64_t)h->p.bin_steps);
+      B.pinned_wins[i].pad = 0;
+    }
+    CU_TRY(cudaMemcpyAsync(B.wins.p, B.pinned_wins, (size_t)n * sizeof(NetWin), cudaMemcpyHostToDevice, s));
+    CU_TRY(cudaGraphLaunch(B.exec, s));
+    for (int i = 0; i < n; ++i) {
+      snn_net *h = hs[i];
+      const uint64_t adv = std::min<uint64_t>(window, left[i]);
+      if (adv == 0) continue;
+      int rc = drain_window(h, h->t, s);
+      if (rc) return rc;
+      h->t += adv;
+      left[i] -= adv;
+    }
+  }
+  return SNN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// public run calls
+// ---------------------------------------------------------------------------
+extern "C" int snn_run(snn_handle h, uint64_t steps) {
+  if (!h) return fail(SNN_ERR_ARG, "null handle");
+  if (h->broken) return fail(SNN_ERR_STATE, "network is invalid after an earlier failure");
+  if (steps == 0) return SNN_OK;
+  if (h->cfg.path == 1) {
+    snn_net *one[1] = {h};
+    return run_fused(one, &steps, 1);
+  }
+  return run_plain(h, steps);
+}
+
+extern "C" int snn_run_batch(const snn_handle *hs, const uint64_t *steps, int32_t n) {
+  if (!hs || !steps || n < 1) return fail(SNN_ERR_ARG, "empty batch");
+  if (n > 65535) return fail(SNN_ERR_LIMIT, "more than 65535 networks in one batch");
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i]) return fail(SNN_ERR_ARG, "null handle in batch");
+    if (hs[i]->broken) return fail(SNN_ERR_STATE, "network is invalid after an earlier failure");
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return fail(SNN_ERR_ARG, "a network appears twice in the batch");
+  }
+  return run_fused(hs, steps, n);
+}
+
+// ---------------------------------------------------------------------------
+// reads
+// ---------------------------------------------------------------------------
+extern "C" int snn_read_spikes(snn_handle h, uint64_t t0, uint64_t t1, uint32_t *step_out, uint32_t *id_out,
+                               size_t cap, size_t *n_out) {
+  if (!h || !n_out) return fail(SNN_ERR_ARG, "null argument");
+  if (h->raster_sorted < h->raster.size()) {
+    // records are appended window by window, so only the new tail needs ordering
+    std::sort(h->raster.begin() + (ptrdiff_t)h->raster_sorted, h->raster.end());
+    h->raster_sorted = h->raster.size();
+  }
+  auto a = t0 > 0xFFFFFFFFull ? h->raster.end()
+                              : std::lower_bound(h->raster.begin(), h->raster.end(), (unsigned long long)(t0 << 32));
+  auto b = t1 > 0xFFFFFFFFull ? h->raster.end()
+                              : std::lower_bound(a, h->raster.end(), (unsigned long long)(t1 << 32));
+  if (t1 <= t0) b = a;
+  const size_t n = (size_t)(b - a);
+  *n_out = n;
+  if (n > cap) return fail(SNN_ERR_BUFFER, "spike buffer too small");
+  if (n && (!step_out || !id_out)) return fail(SNN_ERR_ARG, "null output buffer");
+  size_t i = 0;
+  for (auto it = a; it != b; ++it, ++i) {
+    step_out[i] = (uint32_t)(*it >> 32);
+    id_out[i] = (uint32_t)(*it & 0xFFFFFFFFull);
+  }
+  return SNN_OK;
+}
+
+extern "C" int snn_rates(snn_handle h, uint32_t *counts_out, size_t cap, size_t *n_out) {
+  if (!h || !n_out) return fail(SNN_ERR_ARG, "null argument");
+  const size_t per_bin = (size_t)h->L.G * 3;
+  const uint64_t bins = (h->t + (uint64_t)h->p.bin_steps - 1) / (uint64_t)h->p.bin_steps;
+  const size_t n = (size_t)bins * per_bin;
+  *n_out = n;
+  if (n > cap) return fail(SNN_ERR_BUFFER, "rate buffer too small");
+  if (n && !counts_out) return fail(SNN_ERR_ARG, "null output buffer");
+  for (size_t i = 0; i < n; ++i) counts_out[i] = i < h->rates.size() ? h->rates[i] : 0u;
+  return SNN_OK;
+}
+
+extern "C" int snn_read_state(snn_handle h, float *V_out, float *c_out, int32_t *ref_out, size_t n) {
+  if (!h) return fail(SNN_ERR_ARG, "null handle");
+  const uint32_t N = h->L.N;
+  if (n < N) return fail(SNN_ERR_BUFFER, "state buffers shorter than N");
+  std::vector<uint8_t> ref(N);
+  if (V_out) CU_TRY(cudaMemcpyAsync(V_out, h->hd.V, (size_t)N * 4, cudaMemcpyDeviceToHost, h->stream));
+  if (c_out) CU_TRY(cudaMemcpyAsync(c_out, h->hd.c, (size_t)N * 4, cudaMemcpyDeviceToHost, h->stream));
+  CU_TRY(cudaMemcpyAsync(ref.data(), h->hd.ref, N, cudaMemcpyDeviceToHost, h->stream));
+  CU_TRY(cudaStreamSynchronize(h->stream));
+  if (ref_out)
+    for (uint32_t i = 0; i < N; ++i) ref_out[i] = ref[i];
+  return SNN_OK;
+}
+
+extern "C" int snn_read_row(snn_handle h, uint32_t s, uint32_t *keys_out, float *w_out, size_t cap) {
+  if (!h) return fail(SNN_ERR_ARG, "null handle");
+  if (s >= h->L.N) return fail(SNN_ERR_ARG, "source index out of range");
+  if (cap < h->L.M) return fail(SNN_ERR_BUFFER, "row buffers shorter than M");
+  std::vector<uint8_t> row(h->L.row_bytes);
+  CU_TRY(cudaMemcpyAsync(row.data(), h->hd.rows + (size_t)s * h->L.row_bytes, h->L.row_bytes,
+                         cudaMemcpyDeviceToHost, h->stream));
+  CU_TRY(cudaStreamSynchronize(h->stream));
+  const uint32_t M = h->L.M, Mp = h->L.M_pad;
+  if (keys_out) std::memcpy(keys_out, row.data(), (size_t)M * 4);
+  if (w_out) {
+    if (h->p.record_format == SNN_REC_I16) {
+      const int16_t *q = reinterpret_cast<const int16_t *>(row.data() + (size_t)Mp * 4);
+      for (uint32_t j = 0; j < M; ++j) w_out[j] = (float)q[j] * (1.0f / 1024.0f);
+    } else {
+      std::memcpy(w_out, row.data() + (size_t)Mp * 4, (size_t)M * 4);
+    }
+  }
+  return SNN_OK;
+}
+
+extern "C" int snn_get_stats(snn_handle h, snn_stats *out) {
+  if (!h || !out) return fail(SNN_ERR_ARG, "null argument");
+  out->t = h->t;
+  out->spikes = h->spikes;
+  out->rec_events = h->spikes * (uint64_t)h->L.M;
+  out->ext_events = h->ext_events;
+  out->n_neurons = h->L.N;
+  out->n_synapses = (uint64_t)h->L.N * h->L.M;
+  out->device_bytes = h->arena.bytes;
+  out->record_bytes = (uint64_t)h->L.N * h->L.row_bytes;
+  out->build_ms = h->build_ms;
+  return SNN_OK;
+}
+
+extern "C" int snn_get_launch(snn_handle h, snn_launch *out) {
+  if (!h || !out) return fail(SNN_ERR_ARG, "null argument");
+  *out = h->cfg;
+  return SNN_OK;
+}
+
+extern "C" int snn_set_launch(snn_handle h, const snn_launch *cfg) {
+  if (!h || !cfg) return fail(SNN_ERR_ARG, "null argument");
+  const snn_launch &c = *cfg;
+  if (c.path != 0 && c.path != 1) return fail(SNN_ERR_ARG, "path must be 0 or 1");
+  if (c.update_block != 128 && c.update_block != 256 && c.update_block != 512)
+    return fail(SNN_ERR_ARG, "update_block must be 128, 256 or 512");
+  if (c.deliver_warps < 1 || c.deliver_warps > 8) return fail(SNN_ERR_ARG, "deliver_warps must be in 1..8");
+  if (c.fused_block < 128 || c.fused_block > 512 || c.fused_block % 32)
+    return fail(SNN_ERR_ARG, "fused_block must be a multiple of 32 in 128..512");
+  if (c.fused_items_per_sm < 1 || c.fused_items_per_sm > 8) return fail(SNN_ERR_ARG, "fused_items_per_sm in 1..8");
+  if (c.window_steps < 1 || c.window_steps > 4096) return fail(SNN_ERR_ARG, "window_steps in 1..4096");
+  if (c.deliver_chunk < 8 || c.deliver_chunk % 8 || (uint32_t)c.deliver_chunk > max_chunk_records())
+    return fail(SNN_ERR_ARG, "deliver_chunk must be a multiple of 8 in 8..1152");
+  h->cfg = c;
+  return SNN_OK;
+}
+
+extern "C" int snn_debug_set_wait_limit(snn_handle h, uint32_t iterations) {
+  if (!h) return fail(SNN_ERR_ARG, "null handle");
+  h->wait_limit = iterations;
+  h->hd.wait_limit = iterations;
+  return SNN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: time candidate shapes from a snapshot of the state, restore the
+// snapshot after each trial, so the network's results are unchanged.
+// ---------------------------------------------------------------------------
+extern "C" int snn_autotune(snn_handle h, uint32_t trial_steps) {
+  if (!h) return fail(SNN_ERR_ARG, "null handle");
+  if (h->broken) return fail(SNN_ERR_STATE, "network is invalid after an earlier failure");
+  if (trial_steps == 0) return fail(SNN_ERR_ARG, "trial_steps must be > 0");
+  const Layout &L = h->L;
+  uint8_t *base = static_cast<uint8_t *>(h->arena.p);
+  const size_t state_bytes = L.off_rows;   // V, c, ref, ring
+  DevBuf snap;
+  int rc = dev_alloc(snap, state_bytes);
+  if (rc) return rc;
+  struct G {
+    DevBuf *b;
+    cudaStream_t s;
+    ~G() {
+      cudaStreamSynchronize(s);
+      b->release();
+    }
+  } guard{&snap, h->stream};
+  cudaStream_t s = h->stream;
+  CU_TRY(cudaMemcpyAsync(snap.p, base, state_bytes, cudaMemcpyDeviceToDevice, s));
+  const uint64_t t_saved = h->t, spikes_saved = h->spikes, ext_saved = h->ext_events;
+  const size_t raster_saved = h->raster.size(), sorted_saved = h->raster_sorted;
+  const std::vector<uint32_t> rates_saved = h->rates;
+  const snn_launch orig = h->cfg;
+
+  std::vector<snn_launch> cands;
+  for (int ub : {128, 256, 512})
+    for (int dw : {2, 4, 8})
+      for (int ch : {1152, 576, 384, 192}) {
+        snn_launch c = orig;
+        c.path = 0;
+        c.update_block = ub;
+        c.deliver_warps = dw;
+        c.deliver_chunk = ch;
+        cands.push_back(c);
+      }
+  for (int fb : {128, 256, 512})
+    for (int ips : {1, 2, 4})
+      for (int ch : {576, 288, 144}) {
+        snn_launch c = orig;
+        c.path = 1;
+        c.fused_block = fb;
+        c.fused_items_per_sm = ips;
+        c.deliver_chunk = ch;
+        cands.push_back(c);
+      }
+  cudaEvent_t e0, e1;
+  CU_TRY(cudaEventCreate(&e0));
+  CU_TRY(cudaEventCreate(&e1));
+  float best_ms = 1e30f;
+  snn_launch best = orig;
+  int status = SNN_OK;
+  for (const snn_launch &c : cands) {
+    h->cfg = c;
+    for (int rep = 0; rep < 2 && status == SNN_OK; ++rep) {   // first pass captures the graph
+      CU_TRY(cudaMemcpyAsync(base, snap.p, state_bytes, cudaMemcpyDeviceToDevice, s));
+      h->t = t_saved;
+      CU_TRY(cudaEventRecord(e0, s));
+      int r = snn_run(h, trial_steps);
+      if (r) { status = r; break; }
+      CU_TRY(cudaEventRecord(e1, s));
+      CU_TRY(cudaEventSynchronize(e1));
+      float ms = 0;
+      CU_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      if (rep == 1 && ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+    if (status != SNN_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // restore the network exactly as it was
+  CU_TRY(cudaMemcpyAsync(base, snap.p, state_bytes, cudaMemcpyDeviceToDevice, s));
+  CU_TRY(cudaMemsetAsync(base + L.off_rec, 0, L.off_entries - L.off_rec, s));
+  CU_TRY(cudaStreamSynchronize(s));
+  h->t = t_saved;
+  h->spikes = spikes_saved;
+  h->ext_events = ext_saved;
+  h->raster.resize(raster_saved);
+  h->raster_sorted = std::min(sorted_saved, raster_saved);
+  h->rates = rates_saved;
+  h->cfg = (status == SNN_OK) ? best : orig;
+  return status;
+}

@@ -1,0 +1,112 @@
+// snn_internal.h -- device descriptors shared by the host runtime (snn_host.cpp)
+// and the kernels (snn_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace snn {
+
+constexpr int kK = 1250;          // neurons per module (Sec. 2.2)
+constexpr int kNPop = 3;          // F, B, I
+constexpr int kZTab = 4096;       // Gaussian quantile table size (12-bit index)
+constexpr int kPoisMax = 16;      // external events per neuron and step are capped at 16
+constexpr int kMaxM = 4096;       // out-degree limit
+constexpr int kNeuronAlign = 128; // neuron arrays padded to a multiple of 128
+
+// status bits written by kernels
+constexpr uint32_t kStatusTimeout = 1u;
+constexpr uint32_t kStatusRasterOverflow = 2u;
+
+// Time window of one graph replay (device memory, rewritten by the host
+// before every replay so that captured graphs stay valid).
+struct alignas(16) NetWin {
+  uint32_t t0;          // absolute step of the window's first step
+  uint32_t t_end;       // exclusive absolute step at which the network stops
+  uint32_t bin0;        // first rate bin of the window (t0 / bin_steps)
+  uint32_t pad;
+};
+
+// Recording header of a network (device memory, zeroed at every window start).
+struct alignas(16) RecHeader {
+  uint32_t cursor;        // raster entries appended in this window
+  uint32_t status;        // kStatus* bits
+  uint32_t step_base[2];  // first entry of the step with that parity
+};
+
+// Static description of a network.  Passed by value as a kernel parameter on
+// the single-network path and stored in a device table on the fused path.
+struct alignas(16) NetDev {
+  // --- sizes
+  uint32_t N;           // neurons
+  uint32_t N_pad;       // padded to kNeuronAlign
+  uint32_t G, gx;       // modules, grid width
+  uint32_t M;           // out-degree
+  uint32_t M_pad;       // padded to a multiple of 8
+  uint32_t D;           // ring slots = n_delay + 1
+  uint32_t fmt;         // 0 = f32 weights, 1 = i16 weights
+  uint32_t row_bytes;   // bytes of one row: M_pad keys then M_pad weights
+  uint32_t bin_steps;
+  uint32_t key0, key1;  // Philox key (seed)
+  uint32_t slot;        // index of this network in a batch
+  uint32_t rec_cap;     // raster entries per window
+  uint32_t rates_bins;  // bins in the rate window
+  uint32_t wait_limit;  // bounded-wait iterations
+
+  // --- per population constants (Eq. 2 propagators, Table S1)
+  float pvv[kNPop], pvc[kNPop], pcc[kNPop];
+  float el[kNPop], vth[kNPop], vr[kNPop], alpha[kNPop];
+  int32_t narp[kNPop];
+  uint32_t pad0[2];
+  unsigned long long thr[kNPop][kPoisMax];   // Poisson CDF thresholds (u32 scale)
+
+  // --- device arrays
+  float *V;             // [N_pad]
+  float *c;             // [N_pad]
+  uint8_t *ref;         // [N_pad]
+  int32_t *ring;        // [D][N_pad], 2^-16 mV
+  uint8_t *rows;        // [N][row_bytes]
+  const int32_t *amp;   // [3][kZTab] external amplitudes, 2^-16 mV
+  const NetWin *win;    // current window
+  RecHeader *rec;       // recording header
+  unsigned long long *rec_entries;  // [rec_cap] (slot << 48 | k << 32 | id)
+  uint32_t *rates;      // [rates_bins][G][3] window counts
+  unsigned long long *ext_acc;      // [N_pad / 128] external events per 128-neuron group
+};
+
+// Construction-time inputs.
+struct BuildDev {
+  const uint32_t *cdf;  // [G][G-1] module thresholds
+  const float *ztab;    // [kZTab]
+  float J[kNPop][kNPop];
+  float sig[kNPop][kNPop];
+  uint32_t n_delay;
+  int32_t p_local_mode; // 1 when p_local >= 0 (local bucket shortcut valid), 0 otherwise
+};
+
+// Work item of the fused step kernel: a range of one network's neurons.
+struct FusedItem {
+  uint32_t net;         // index into the NetDev table
+  uint32_t n_begin;     // first neuron (multiple of 4)
+};
+
+struct FusedTable {
+  const NetDev *nets;
+  const FusedItem *items;
+  uint32_t n_items;
+  uint32_t chunk;       // records per delivery chunk
+};
+
+// ---- launchers (snn_kernels.cu) -------------------------------------------
+cudaError_t prepare_kernels();
+cudaError_t launch_build_rows(const NetDev &h_nd, const BuildDev &bd, cudaStream_t s);
+cudaError_t launch_init_state(const NetDev &nd, cudaStream_t s);
+cudaError_t launch_update(const NetDev &nd, uint32_t k, int block, cudaStream_t s);
+cudaError_t launch_deliver(const NetDev &nd, uint32_t k, uint32_t chunk, int warps, int blocks, cudaStream_t s);
+cudaError_t launch_fused(const FusedTable &tab, uint32_t k, int block, int blocks, cudaStream_t s);
+uint32_t max_chunk_records();        // largest chunk of the two-kernel delivery
+uint32_t max_fused_chunk_records();  // largest chunk of the fused step
+int device_sm_count();
+
+}  // namespace snn

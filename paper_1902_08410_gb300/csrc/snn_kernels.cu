@@ -1,0 +1,688 @@
+// snn_kernels.cu -- sm_103a kernels of the DPSNN-style grid simulation.
+//
+// Arithmetic contract (identical on every path, no FMA contraction: the
+// dynamics use explicit __fmul_rn/__fadd_rn and the file is built with
+// -fmad=false):
+//   Eq. 2 over one step for neuron n at step t (slot st = t mod D):
+//     I  = ring[st][n]; ring[st][n] = 0
+//     r  = Philox4x32-10(key = seed, ctr = (n, t, 1, 0))
+//     k  = #{j < 16 : r.x >= thr[pop][j]}           (Poisson count, Sec. 2.1)
+//     I += amp[pop][half_e >> 4] for the k external events
+//     ref > 0 : ref -= 1, V = V_r                    (refractory clamp, Sec. 2.2)
+//     else    : V = (E + (P_VV*(V-E) + P_Vc*c)) + I*2^-16; spike if V > V_th
+//     c = P_cc*c (+ alpha when the neuron fired)
+//   Delivery of a spike of step t: every record (d, target, w) of the source's
+//   row adds its fixed-point weight to ring[(t+d) mod D][target] (int32 atomics,
+//   so the sum does not depend on order).
+#include <algorithm>
+#include <cstdint>
+
+#include "snn_internal.h"
+
+namespace snn {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds, Weyl key schedule.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                               uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c0;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0;
+    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+__device__ __forceinline__ int pop_of_local(uint32_t local) { return local < 250u ? 0 : (local < 1000u ? 1 : 2); }
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// ---------------------------------------------------------------------------
+// Asynchronous bulk copies (TMA, non-tensor) into shared memory with mbarriers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar,
+                                         uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(bar), "l"(pol)
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: at most `limit` polls (each poll may suspend briefly).
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+constexpr uint32_t kDefaultWaitLimit = 1u << 22;
+
+// ---------------------------------------------------------------------------
+// Fire-and-forget global reductions (no value returned, no scoreboard wait).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void red_add_s32(int32_t *addr, int32_t v) {
+  asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_u32(uint32_t *addr, uint32_t v) {
+  asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(addr), "r"(v) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Neuron update (Eq. 2 over one step, Poisson drive) of 4 consecutive neurons.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t poisson_count(const NetDev &nd, int pop, uint32_t u) {
+  uint32_t k = 0;
+  while (k < (uint32_t)kPoisMax && (unsigned long long)u >= nd.thr[pop][k]) ++k;
+  return k;
+}
+
+// Sum of the amplitudes of k external events of neuron n at step t (2^-16 mV).
+__device__ __noinline__ int32_t external_amplitudes(const NetDev &nd, int pop, const uint4 r, uint32_t k, uint32_t n,
+                                                    uint32_t t) {
+  const int32_t *ap = nd.amp + pop * kZTab;
+  int32_t I = 0;
+  for (uint32_t e = 0; e < k; ++e) {
+    uint32_t word, hi;
+    if (e < 6u) {
+      const uint32_t w = e >> 1;
+      word = (w == 0) ? r.y : ((w == 1) ? r.z : r.w);
+      hi = e & 1u;
+    } else {
+      const uint32_t ee = e - 6u;
+      const uint4 q = philox4x32_10(n, t, 1u, 1u + ee / 8u, nd.key0, nd.key1);
+      const uint32_t w = (ee % 8u) >> 1;
+      word = (w == 0) ? q.x : ((w == 1) ? q.y : ((w == 2) ? q.z : q.w));
+      hi = ee & 1u;
+    }
+    const uint32_t half = hi ? (word >> 16) : (word & 0xFFFFu);
+    I += __ldg(ap + (half >> 4));
+  }
+  return I;
+}
+
+__device__ __forceinline__ bool neuron_step(const NetDev &nd, int pop, float &V, float &c, uint32_t &ref, int32_t I) {
+  bool spike = false;
+  const float c_old = c;
+  if (ref > 0u) {
+    ref -= 1u;
+    V = nd.vr[pop];
+  } else {
+    const float el = nd.el[pop];
+    const float a = __fsub_rn(V, el);
+    const float b = __fmul_rn(nd.pvv[pop], a);
+    const float e = __fmul_rn(nd.pvc[pop], c_old);
+    const float f = __fadd_rn(b, e);
+    const float g = __fadd_rn(el, f);
+    const float x = __fmul_rn(__int2float_rn(I), 1.0f / 65536.0f);
+    float vn = __fadd_rn(g, x);
+    if (vn > nd.vth[pop]) {
+      spike = true;
+      vn = nd.vr[pop];
+      ref = (uint32_t)nd.narp[pop];
+    }
+    V = vn;
+  }
+  float cn = __fmul_rn(nd.pcc[pop], c_old);
+  if (spike) cn = __fadd_rn(cn, nd.alpha[pop]);
+  c = cn;
+  return spike;
+}
+
+// Update neurons n0..n0+3 (n0 % 4 == 0, n0 < N_pad) at step t; returns the
+// 4-bit spike mask and adds the number of external events to n_ext.
+__device__ __forceinline__ uint32_t update4(const NetDev &nd, uint32_t n0, uint32_t t, uint32_t &n_ext) {
+  const uint32_t i4 = n0 >> 2;
+  const uint32_t st = t % nd.D;
+  const float4 V4 = reinterpret_cast<const float4 *>(nd.V)[i4];
+  const float4 c4 = reinterpret_cast<const float4 *>(nd.c)[i4];
+  const uchar4 r4 = reinterpret_cast<const uchar4 *>(nd.ref)[i4];
+  int4 *slot = reinterpret_cast<int4 *>(nd.ring + (size_t)st * nd.N_pad);
+  const int4 I4 = slot[i4];
+  slot[i4] = make_int4(0, 0, 0, 0);
+  // the four counter-based draws are independent: issue them together
+  uint4 R[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) R[q] = philox4x32_10(n0 + q, t, 1u, 0u, nd.key0, nd.key1);
+  uint32_t local = n0 % (uint32_t)kK;
+  int pops[4];
+  uint32_t kx[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    pops[q] = pop_of_local(local);
+    kx[q] = poisson_count(nd, pops[q], R[q].x);
+    local = (local + 1u == (uint32_t)kK) ? 0u : local + 1u;
+  }
+  int32_t Iv[4] = {I4.x, I4.y, I4.z, I4.w};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (kx[q]) Iv[q] += external_amplitudes(nd, pops[q], R[q], kx[q], n0 + q, t);
+  }
+  float Vv[4] = {V4.x, V4.y, V4.z, V4.w};
+  float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+  uint32_t rv[4] = {r4.x, r4.y, r4.z, r4.w};
+  uint32_t mask = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (n0 + q < nd.N) {
+      n_ext += kx[q];
+      if (neuron_step(nd, pops[q], Vv[q], cv[q], rv[q], Iv[q])) mask |= 1u << q;
+    }
+  }
+  if (n0 < nd.N) {
+    reinterpret_cast<float4 *>(nd.V)[i4] = make_float4(Vv[0], Vv[1], Vv[2], Vv[3]);
+    reinterpret_cast<float4 *>(nd.c)[i4] = make_float4(cv[0], cv[1], cv[2], cv[3]);
+    reinterpret_cast<uchar4 *>(nd.ref)[i4] =
+        make_uchar4((unsigned char)rv[0], (unsigned char)rv[1], (unsigned char)rv[2], (unsigned char)rv[3]);
+  }
+  return mask;
+}
+
+// Warp-level recording of the warp's spikes (all 32 lanes active; lane L owns
+// neurons n0..n0+3).  Appends raster entries with one returning atomic per
+// warp, counts rates with fire-and-forget reductions, and adds the warp's
+// external events to its own 128-neuron slot.  When `smem_list` is given the
+// ids are also appended there (block-local list for fused delivery).
+__device__ __forceinline__ void record_warp(const NetDev &nd, uint32_t mask, uint32_t n0, uint32_t t, uint32_t k,
+                                            uint32_t bin0, uint32_t n_ext, uint32_t *smem_list,
+                                            uint32_t *smem_count) {
+  const uint32_t lane = lane_id();
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t before = 0, wtot = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint32_t b = __ballot_sync(0xFFFFFFFFu, (mask >> q) & 1u);
+    before += __popc(b & lt);
+    wtot += __popc(b);
+  }
+  uint32_t ext = n_ext;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ext += __shfl_xor_sync(0xFFFFFFFFu, ext, o);
+  const uint32_t n_first = __shfl_sync(0xFFFFFFFFu, n0, 0);
+  if (lane == 0 && ext) nd.ext_acc[n_first >> 7] += ext;   // slot owned by this warp
+  if (wtot == 0) return;
+  uint32_t gbase = 0, sbase = 0;
+  if (lane == 0) {
+    gbase = atomicAdd(&nd.rec->cursor, wtot);
+    if (smem_list) sbase = atomicAdd(smem_count, wtot);
+  }
+  gbase = __shfl_sync(0xFFFFFFFFu, gbase, 0);
+  sbase = __shfl_sync(0xFFFFFFFFu, sbase, 0);
+  if (lane == 0 && gbase + wtot > nd.rec_cap) atomicOr(&nd.rec->status, kStatusRasterOverflow);
+  const unsigned long long tag = ((unsigned long long)nd.slot << 48) | ((unsigned long long)k << 32);
+  const uint32_t bin = t / nd.bin_steps - bin0;
+  uint32_t pos = before;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if ((mask >> q) & 1u) {
+      const uint32_t id = n0 + q;
+      if (gbase + pos < nd.rec_cap) nd.rec_entries[gbase + pos] = tag | id;
+      if (smem_list) smem_list[sbase + pos] = id;
+      const uint32_t m = id / (uint32_t)kK;
+      red_add_u32(nd.rates + ((size_t)bin * nd.G + m) * 3u + pop_of_local(id - m * (uint32_t)kK), 1u);
+      ++pos;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Delivery: warps take work items (spike, chunk of its row); the chunk's keys
+// and weights are staged in shared memory by bulk asynchronous copies (TMA),
+// double buffered with one mbarrier per buffer, then scattered into the ring
+// with fire-and-forget int32 reductions.
+// ---------------------------------------------------------------------------
+struct WarpStage {
+  uint8_t *buf0, *buf1;  // chunk buffers: keys, then weights
+  uint32_t bar0, bar1;   // mbarrier shared addresses
+  uint32_t ph0, ph1;     // phase parity per buffer
+  uint32_t cap;          // records the buffers hold
+};
+
+__device__ __forceinline__ void init_stage(WarpStage &ws, uint8_t *base, uint64_t *bars, uint32_t cap) {
+  ws.buf0 = base;
+  ws.buf1 = base + (size_t)cap * 8u;
+  ws.bar0 = smem_u32(bars);
+  ws.bar1 = smem_u32(bars + 1);
+  ws.ph0 = ws.ph1 = 0u;
+  ws.cap = cap;
+  if (lane_id() == 0) {
+    mbar_init(ws.bar0, 1);
+    mbar_init(ws.bar1, 1);
+    fence_mbar_init();
+    fence_proxy_async_smem();
+  }
+  __syncwarp();
+}
+
+// Issue the copy of records [j0, j0 + n) of row `src` into buffer b (leader lane).
+__device__ __forceinline__ void issue_chunk(const NetDev &nd, uint8_t *buf, uint32_t bar, uint32_t chunk,
+                                            uint32_t src, uint32_t j0, uint64_t pol) {
+  const uint32_t n = min(chunk, nd.M_pad - j0);
+  const uint32_t wb = nd.fmt ? 2u : 4u;
+  const uint8_t *row = nd.rows + (size_t)src * nd.row_bytes;
+  const uint32_t kbytes = n * 4u, wbytes = n * wb;
+  mbar_expect_tx(bar, kbytes + wbytes);
+  bulk_g2s(smem_u32(buf), row + (size_t)j0 * 4u, kbytes, bar, pol);
+  bulk_g2s(smem_u32(buf + (size_t)chunk * 4u), row + (size_t)nd.M_pad * 4u + (size_t)j0 * wb, wbytes, bar, pol);
+}
+
+__device__ __forceinline__ void scatter_chunk(const NetDev &nd, const uint8_t *buf, uint32_t chunk, uint32_t j0,
+                                              uint32_t st) {
+  const uint32_t nvalid = j0 < nd.M ? min(chunk, nd.M - j0) : 0u;
+  const uint32_t *keys = reinterpret_cast<const uint32_t *>(buf);
+  const uint8_t *wbase = buf + (size_t)chunk * 4u;
+  int32_t *ring = nd.ring;
+  const uint32_t D = nd.D;
+  const size_t npad = nd.N_pad;
+  if (nd.fmt) {
+    const int16_t *wq = reinterpret_cast<const int16_t *>(wbase);
+    for (uint32_t i = lane_id(); i < nvalid; i += 32u) {
+      const uint32_t key = keys[i];
+      uint32_t slot = st + (key >> 24);
+      slot = slot >= D ? slot - D : slot;
+      red_add_s32(ring + (size_t)slot * npad + (key & 0xFFFFFFu), (int32_t)wq[i] * 64);
+    }
+  } else {
+    const float *wf = reinterpret_cast<const float *>(wbase);
+    for (uint32_t i = lane_id(); i < nvalid; i += 32u) {
+      const uint32_t key = keys[i];
+      uint32_t slot = st + (key >> 24);
+      slot = slot >= D ? slot - D : slot;
+      red_add_s32(ring + (size_t)slot * npad + (key & 0xFFFFFFu), __float2int_rn(__fmul_rn(wf[i], 65536.0f)));
+    }
+  }
+}
+
+// Deliver work items first, first + stride, ... < n_items, where item i is
+// chunk (i % nch) of the row of source src_of(i / nch).  Returns false when a
+// bounded wait gave up (the status bit is set; copies in flight are drained).
+template <typename SrcOf>
+__device__ bool deliver_items(const NetDev &nd, WarpStage &ws, uint32_t chunk, uint32_t first, uint32_t stride,
+                              uint32_t n_items, uint32_t st, SrcOf src_of) {
+  if (first >= n_items) return true;
+  const uint32_t nch = (nd.M_pad + chunk - 1u) / chunk;
+  const uint64_t pol = l2_evict_first_policy();
+  const bool leader = lane_id() == 0;
+  if (leader) issue_chunk(nd, ws.buf0, ws.bar0, chunk, src_of(first / nch), (first % nch) * chunk, pol);
+  uint32_t b = 0;
+  for (uint32_t i = first; i < n_items; i += stride) {
+    const uint32_t nxt = i + stride;
+    if (nxt < n_items && leader) {
+      if (b == 0) issue_chunk(nd, ws.buf1, ws.bar1, chunk, src_of(nxt / nch), (nxt % nch) * chunk, pol);
+      else issue_chunk(nd, ws.buf0, ws.bar0, chunk, src_of(nxt / nch), (nxt % nch) * chunk, pol);
+    }
+    const uint32_t bar = b ? ws.bar1 : ws.bar0;
+    const uint32_t ph = b ? ws.ph1 : ws.ph0;
+    bool got = mbar_wait_bounded(bar, ph, nd.wait_limit);
+    got = __all_sync(0xFFFFFFFFu, got);
+    if (!got) {
+      if (leader) atomicOr(&nd.rec->status, kStatusTimeout);
+      mbar_wait_bounded(bar, ph, kDefaultWaitLimit);
+      if (nxt < n_items) mbar_wait_bounded(b ? ws.bar0 : ws.bar1, b ? ws.ph0 : ws.ph1, kDefaultWaitLimit);
+      return false;
+    }
+    if (b) ws.ph1 ^= 1u; else ws.ph0 ^= 1u;
+    scatter_chunk(nd, b ? ws.buf1 : ws.buf0, chunk, (i % nch) * chunk, st);
+    __syncwarp();
+    fence_proxy_async_smem();   // our reads of this buffer precede its next async refill
+    __syncwarp();
+    b ^= 1u;
+  }
+  return true;
+}
+
+constexpr uint32_t kStageCap = 1152;   // records per staging buffer of k_deliver (f32: 9216 B)
+constexpr uint32_t kFusedCap = 576;    // records per staging buffer of k_fused
+
+uint32_t max_chunk_records() { return kStageCap; }
+uint32_t max_fused_chunk_records() { return kFusedCap; }
+
+// ---------------------------------------------------------------------------
+// Kernel: initial state (V uniform on [0, V_th) from Philox stream 2).
+// ---------------------------------------------------------------------------
+__global__ void k_init_state(const __grid_constant__ NetDev nd) {
+  const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nd.N_pad) return;
+  float v = 0.0f;
+  if (n < nd.N) {
+    const uint4 r = philox4x32_10(n, 0u, 2u, 0u, nd.key0, nd.key1);
+    const float u = __fmul_rn(__uint2float_rn(r.x >> 8), 1.0f / 16777216.0f);
+    v = __fmul_rn(nd.vth[pop_of_local(n % (uint32_t)kK)], u);
+  }
+  nd.V[n] = v;
+  nd.c[n] = 0.0f;
+  nd.ref[n] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel: synapse rows (Eq. 1 module choice, uniform target within the module,
+// uniform delay, Gaussian efficacy), each row stable-sorted by delay.
+// Grid (G, 5): block (m, y) builds rows of module m, local indices
+// [250 y, 250 y + 250).  One warp per row at a time.
+// ---------------------------------------------------------------------------
+constexpr int kBuildWarpsMax = 8;
+
+__global__ void __launch_bounds__(kBuildWarpsMax * 32) k_build_rows(NetDev nd, BuildDev bd, uint32_t cdf_in_smem) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  float *s_z = reinterpret_cast<float *>(smem);                       // kZTab
+  uint32_t *s_cdf = reinterpret_cast<uint32_t *>(s_z + kZTab);        // G-1 (if staged)
+  const uint32_t Gm1 = nd.G - 1u;
+  const uint32_t cdf_words = cdf_in_smem ? ((Gm1 + 3u) & ~3u) : 0u;
+  uint8_t *warp_base = reinterpret_cast<uint8_t *>(s_cdf + cdf_words);
+  const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+  const uint32_t per_warp = nd.M_pad * 10u + 256u * 4u;   // keys, weights, perm (u16), counts
+  uint32_t *w_key = reinterpret_cast<uint32_t *>(warp_base + (size_t)warp * per_warp);
+  float *w_w = reinterpret_cast<float *>(w_key + nd.M_pad);
+  uint32_t *w_cnt = reinterpret_cast<uint32_t *>(w_w + nd.M_pad);     // 256 counters
+  uint16_t *w_perm = reinterpret_cast<uint16_t *>(w_cnt + 256);
+
+  const uint32_t m = blockIdx.x;
+  for (uint32_t i = threadIdx.x; i < (uint32_t)kZTab; i += blockDim.x) s_z[i] = bd.ztab[i];
+  const uint32_t *cdf_row = bd.cdf + (size_t)m * Gm1;
+  if (cdf_in_smem)
+    for (uint32_t i = threadIdx.x; i < Gm1; i += blockDim.x) s_cdf[i] = cdf_row[i];
+  __syncthreads();
+  const uint32_t *T = cdf_in_smem ? s_cdf : cdf_row;
+  // local bucket of the source module: [T[m-1], T[m])
+  const unsigned long long lo_loc = (m == 0u) ? 0ull : (unsigned long long)T[m - 1u];
+  const unsigned long long hi_loc = (m == Gm1) ? (1ull << 32) : (unsigned long long)T[m];
+
+  const uint32_t M = nd.M, Mp = nd.M_pad, nd_del = bd.n_delay;
+  const uint32_t n_warps = blockDim.x >> 5;
+  for (uint32_t l = blockIdx.y * 250u + warp; l < blockIdx.y * 250u + 250u; l += n_warps) {
+    const uint32_t s = m * (uint32_t)kK + l;
+    const int sp = pop_of_local(l);
+    for (uint32_t i = lane; i < 256u; i += 32u) w_cnt[i] = 0u;
+    __syncwarp();
+    // 1. draw the M synapses of row s
+    for (uint32_t j = lane; j < M; j += 32u) {
+      const uint4 r = philox4x32_10(s, j, 0u, 0u, nd.key0, nd.key1);
+      uint32_t mt;
+      if (sp == 2 || nd.G == 1u) {
+        mt = m;
+      } else if ((unsigned long long)r.x >= lo_loc && (unsigned long long)r.x < hi_loc) {
+        mt = m;
+      } else {
+        uint32_t lo = 0, hi = Gm1;
+        while (lo < hi) {
+          const uint32_t mid = lo + ((hi - lo) >> 1);
+          if (r.x < T[mid]) hi = mid; else lo = mid + 1u;
+        }
+        mt = lo;
+      }
+      const uint32_t lt = __umulhi(r.y, (uint32_t)kK);
+      const uint32_t tgt = mt * (uint32_t)kK + lt;
+      const uint32_t d = 1u + __umulhi(r.z, nd_del);
+      const int tp = pop_of_local(lt);
+      const float J = bd.J[tp][sp];
+      float w = __fadd_rn(J, __fmul_rn(bd.sig[tp][sp], s_z[r.w >> 20]));
+      if (J > 0.0f && w < 0.0f) w = 0.0f;
+      if (J < 0.0f && w > 0.0f) w = 0.0f;
+      w_key[j] = (d << 24) | tgt;
+      w_w[j] = w;
+      atomicAdd(&w_cnt[d], 1u);
+    }
+    __syncwarp();
+    // 2. exclusive scan of the delay counts (256 entries, 8 per lane)
+    {
+      uint32_t v[8], sum = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        v[q] = w_cnt[lane * 8 + q];
+        sum += v[q];
+      }
+      uint32_t incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= (uint32_t)o) incl += y;
+      }
+      uint32_t acc = incl - sum;
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        w_cnt[lane * 8 + q] = acc;
+        acc += v[q];
+      }
+    }
+    __syncwarp();
+    // 3. stable placement by delay, draws visited in index order
+    for (uint32_t j0 = 0; j0 < M; j0 += 32u) {
+      const uint32_t j = j0 + lane;
+      const bool valid = j < M;
+      const uint32_t d = valid ? (w_key[j] >> 24) : (0x100u + lane);
+      const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+      const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+      uint32_t pos = 0;
+      if (valid) {
+        pos = w_cnt[d] + rank;
+        w_perm[pos] = (uint16_t)j;
+      }
+      __syncwarp();
+      if (valid && (__ffs(peers) - 1) == (int)lane) w_cnt[d] += __popc(peers);
+      __syncwarp();
+    }
+    // 4. write the row: keys then weights, padding records zero
+    uint8_t *row = nd.rows + (size_t)s * nd.row_bytes;
+    uint32_t *okey = reinterpret_cast<uint32_t *>(row);
+    for (uint32_t p = lane; p < Mp; p += 32u) okey[p] = p < M ? w_key[w_perm[p]] : 0u;
+    if (nd.fmt) {
+      int16_t *ow = reinterpret_cast<int16_t *>(row + (size_t)Mp * 4u);
+      for (uint32_t p = lane; p < Mp; p += 32u) {
+        int q = 0;
+        if (p < M) {
+          q = __float2int_rn(__fmul_rn(w_w[w_perm[p]], 1024.0f));
+          q = q > 32767 ? 32767 : (q < -32768 ? -32768 : q);
+        }
+        ow[p] = (int16_t)q;
+      }
+    } else {
+      float *ow = reinterpret_cast<float *>(row + (size_t)Mp * 4u);
+      for (uint32_t p = lane; p < Mp; p += 32u) ow[p] = p < M ? w_w[w_perm[p]] : 0.0f;
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Kernel: neuron update + recording (two-kernel path).  No block barrier:
+// spikes are appended per warp.
+// ---------------------------------------------------------------------------
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_update(const __grid_constant__ NetDev nd, uint32_t k) {
+  const uint32_t n0 = (blockIdx.x * BLOCK + threadIdx.x) * 4u;
+  const uint32_t warp_first = (blockIdx.x * BLOCK + (threadIdx.x & ~31u)) * 4u;
+  if (warp_first >= nd.N_pad) return;   // whole warps: N_pad is a multiple of 128
+  const NetWin w = *nd.win;
+  const uint32_t t = w.t0 + k;
+  if (t >= w.t_end) return;
+  uint32_t n_ext = 0;
+  const uint32_t mask = update4(nd, n0, t, n_ext);
+  record_warp(nd, mask, n0, t, k, w.bin0, n_ext, nullptr, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Kernel: spike delivery of step t (two-kernel path).  The step's spikes are
+// the raster entries [step_base, cursor) appended by k_update.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_deliver(const __grid_constant__ NetDev nd, uint32_t k, uint32_t chunk) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ uint64_t s_bars[16];
+  const NetWin w = *nd.win;
+  const uint32_t t = w.t0 + k;
+  if (t >= w.t_end) return;
+  const uint32_t cur = min(nd.rec->cursor, nd.rec_cap);
+  const uint32_t base = nd.rec->step_base[t & 1u];
+  if (blockIdx.x == 0 && threadIdx.x == 0) nd.rec->step_base[(t + 1u) & 1u] = cur;
+  const uint32_t count = cur > base ? cur - base : 0u;
+  const uint32_t nch = (nd.M_pad + chunk - 1u) / chunk;
+  const uint32_t n_items = count * nch;
+  const uint32_t warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t gwarp = blockIdx.x * nw + warp, total = gridDim.x * nw;
+  if (gwarp >= n_items) return;
+  WarpStage ws;
+  init_stage(ws, smem + (size_t)warp * 2u * kStageCap * 8u, s_bars + 2 * warp, kStageCap);
+  const unsigned long long *ent = nd.rec_entries + base;
+  deliver_items(nd, ws, chunk, gwarp, total, n_items, t % nd.D,
+                [&](uint32_t s) { return (uint32_t)(ent[s] & 0xFFFFFFFFull); });
+}
+
+// ---------------------------------------------------------------------------
+// Kernel: fused step over a table of networks.  A block takes work items
+// (network, 4*blockDim neurons): update, recording and a block-local spike
+// list, then its warps deliver those spikes.  Update reads ring slot t and
+// delivery writes slots t+1..t+D-1, so blocks need no grid-wide barrier.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) k_fused(const __grid_constant__ FusedTable tab, uint32_t k) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ NetDev nd;
+  __shared__ uint64_t s_bars[32];
+  __shared__ uint32_t s_count;
+  __shared__ uint32_t s_net;
+  const uint32_t npi = 4u * blockDim.x;
+  uint32_t *s_ids = reinterpret_cast<uint32_t *>(smem);
+  uint8_t *stage_base = smem + (size_t)npi * 4u;
+  const uint32_t warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  WarpStage ws;
+  init_stage(ws, stage_base + (size_t)warp * 2u * kFusedCap * 8u, s_bars + 2 * warp, kFusedCap);
+  if (threadIdx.x == 0) s_net = 0xFFFFFFFFu;
+  for (uint32_t it = blockIdx.x; it < tab.n_items; it += gridDim.x) {
+    const FusedItem item = tab.items[it];
+    __syncthreads();   // the previous item is done with shared memory
+    if (s_net != item.net) {
+      const uint32_t *src = reinterpret_cast<const uint32_t *>(tab.nets + item.net);
+      uint32_t *dst = reinterpret_cast<uint32_t *>(&nd);
+      for (uint32_t i = threadIdx.x; i < sizeof(NetDev) / 4; i += blockDim.x) dst[i] = src[i];
+    }
+    if (threadIdx.x == 0) s_count = 0u;
+    __syncthreads();
+    if (threadIdx.x == 0) s_net = item.net;
+    const NetWin w = *nd.win;
+    const uint32_t t = w.t0 + k;
+    if (t >= w.t_end) continue;
+    const uint32_t n0 = item.n_begin + threadIdx.x * 4u;
+    const uint32_t warp_first = item.n_begin + warp * 128u;
+    if (warp_first < nd.N_pad) {
+      uint32_t n_ext = 0;
+      const uint32_t mask = update4(nd, n0, t, n_ext);
+      record_warp(nd, mask, n0, t, k, w.bin0, n_ext, s_ids, &s_count);
+    }
+    __syncthreads();
+    const uint32_t cnt = s_count;
+    if (cnt == 0) continue;
+    const uint32_t nch = (nd.M_pad + tab.chunk - 1u) / tab.chunk;
+    deliver_items(nd, ws, tab.chunk, warp, nw, cnt * nch, t % nd.D, [&](uint32_t s) { return s_ids[s]; });
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+int device_sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return sms;
+}
+
+static size_t deliver_smem_bytes(int warps) { return (size_t)warps * 2u * kStageCap * 8u; }
+static size_t fused_smem_bytes(int block) { return (size_t)block * 16u + (size_t)(block / 32) * 2u * kFusedCap * 8u; }
+
+cudaError_t prepare_kernels() {
+  cudaError_t e = cudaFuncSetAttribute(k_deliver, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)deliver_smem_bytes(8));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem_bytes(512));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_build_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+cudaError_t launch_init_state(const NetDev &nd, cudaStream_t s) {
+  const uint32_t threads = 256;
+  const uint32_t blocks = (nd.N_pad + threads - 1) / threads;
+  k_init_state<<<blocks, threads, 0, s>>>(nd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_rows(const NetDev &h_nd, const BuildDev &bd, cudaStream_t s) {
+  const uint32_t Gm1 = h_nd.G - 1u;
+  const uint32_t cdf_in_smem = (Gm1 <= 12288u) ? 1u : 0u;
+  const size_t per_warp = (size_t)h_nd.M_pad * 10u + 256u * 4u;
+  const size_t fixed = (size_t)kZTab * 4u + (cdf_in_smem ? (((size_t)Gm1 + 3u) & ~(size_t)3u) * 4u : 0u);
+  const size_t budget = 200u * 1024u;
+  if (fixed + per_warp > budget) return cudaErrorInvalidValue;
+  const int warps = (int)std::min<size_t>(kBuildWarpsMax, (budget - fixed) / per_warp);
+  const size_t smem = fixed + per_warp * (size_t)warps;
+  dim3 grid(h_nd.G, 5);
+  k_build_rows<<<grid, warps * 32, smem, s>>>(h_nd, bd, cdf_in_smem);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update(const NetDev &nd, uint32_t k, int block, cudaStream_t s) {
+  const uint32_t threads_needed = nd.N_pad / 4u;
+  const uint32_t blocks = (threads_needed + block - 1) / block;
+  switch (block) {
+    case 128: k_update<128><<<blocks, 128, 0, s>>>(nd, k); break;
+    case 256: k_update<256><<<blocks, 256, 0, s>>>(nd, k); break;
+    case 512: k_update<512><<<blocks, 512, 0, s>>>(nd, k); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_deliver(const NetDev &nd, uint32_t k, uint32_t chunk, int warps, int blocks, cudaStream_t s) {
+  if (warps < 1 || warps > 8 || chunk < 8 || chunk > kStageCap || (chunk % 8)) return cudaErrorInvalidValue;
+  k_deliver<<<blocks, warps * 32, deliver_smem_bytes(warps), s>>>(nd, k, chunk);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fused(const FusedTable &tab, uint32_t k, int block, int blocks, cudaStream_t s) {
+  if (block < 128 || block > 512 || (block % 32)) return cudaErrorInvalidValue;
+  if (tab.chunk < 8 || tab.chunk > kFusedCap || (tab.chunk % 8)) return cudaErrorInvalidValue;
+  k_fused<<<blocks, block, fused_smem_bytes(block), s>>>(tab, k);
+  return cudaGetLastError();
+}
+
+}  // namespace snn

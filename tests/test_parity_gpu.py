@@ -1,0 +1,229 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Spike rasters, synapse rows, rate counts, counters and the refractory state are
+integer results and must match bit for bit.  V and c are binary32 results of
+the same operation sequence on both sides; the bar is |a - b| <= 1e-6 * max(1, |b|)
+(identical bits are expected: both sides round every operation once, with no
+fused multiply-add).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def snn():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_1902_08410_gb300 as snn
+    snn.build()
+    return snn
+
+
+def _oracle(oracle_mod, params, seed, steps):
+    o = oracle_mod.OracleNet(params, seed)
+    o.run(steps)
+    return o
+
+
+def _assert_same_run(g, o, steps):
+    gt, gi = g.spikes()
+    ot, oi = o.raster()
+    assert len(gt) == len(ot), (len(gt), len(ot))
+    assert np.array_equal(gt, ot) and np.array_equal(gi, oi)
+    gr, orr = g.rates(), o.rates()
+    assert np.array_equal(gr, orr)
+    gV, gc, gref = g.state()
+    oV, oc, oref = o.state()
+    assert np.array_equal(gref, oref)
+    tolV = 1e-6 * np.maximum(1.0, np.abs(oV))
+    tolc = 1e-6 * np.maximum(1.0, np.abs(oc))
+    assert np.all(np.abs(gV - oV) <= tolV)
+    assert np.all(np.abs(gc - oc) <= tolc)
+    gs, oc_ = g.stats(), o.counters()
+    assert gs["spikes"] == oc_["spikes"] and gs["ext_events"] == oc_["ext_events"]
+    assert gs["rec_events"] == oc_["rec_events"] and gs["t"] == steps
+
+
+# ---------------------------------------------------------------------------
+# construction (Eq. 1 rows) -- bit-exact
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("case", [
+    dict(g=(2, 2), lam=0.4, pl=0.8, fmt=W.REC_F32),
+    dict(g=(3, 2), lam=1.0, pl=0.8, fmt=W.REC_I16),
+    dict(g=(5, 5), lam=0.6, pl=-1.0, fmt=W.REC_F32),
+    dict(g=(1, 1), lam=0.4, pl=0.8, fmt=W.REC_F32),
+])
+def test_rows_bit_exact(snn, oracle_mod, case):
+    p = W.base_params(*case["g"], case["lam"], record_format=case["fmt"], p_local=case["pl"])
+    g = snn.Network(p, 17)
+    o = oracle_mod.OracleNet(p, 17)
+    N = g.N
+    rng = np.random.default_rng(0)
+    sample = np.unique(np.concatenate([[0, 249, 250, 999, 1000, 1249, N - 1], rng.integers(0, N, 60)]))
+    for s in sample:
+        gk, gw = g.row(int(s))
+        ok, ow = o.row(int(s))
+        assert np.array_equal(gk, ok), s
+        if case["fmt"] == W.REC_I16:
+            q = np.clip(np.rint(ow * np.float32(1024.0)), -32768, 32767).astype(np.float32) / np.float32(1024.0)
+            assert np.array_equal(gw, q), s
+        else:
+            assert np.array_equal(gw, ow), s
+    g.close()
+
+
+def test_rows_bit_exact_full_size_sample(snn, oracle_mod):
+    """24x24 grid (720k neurons, 0.81G synapses): sampled rows."""
+    p = W.base_params(24, 24, 1.0)
+    g = snn.Network(p, 1)
+    o = oracle_mod.OracleNet(p, 1)
+    rng = np.random.default_rng(1)
+    for s in np.concatenate([[0, g.N - 1], rng.integers(0, g.N, 40)]):
+        gk, gw = g.row(int(s))
+        ok, ow = o.row(int(s))
+        assert np.array_equal(gk, ok) and np.array_equal(gw, ow), s
+    g.close()
+
+
+# ---------------------------------------------------------------------------
+# whole runs -- raster bit-exact
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("path", [0, 1])
+@pytest.mark.parametrize("fmt", [W.REC_F32, W.REC_I16])
+def test_run_4x4_swa(snn, oracle_mod, path, fmt):
+    p = W.base_params(4, 4, 0.4, "SWA", record_format=fmt)
+    steps = 3000
+    g = snn.Network(p, 1)
+    g.launch = {"path": path}
+    g.run(1234)
+    g.run(steps - 1234)       # two calls: windows and rate bins restart mid-bin
+    o = _oracle(oracle_mod, p, 1, steps)
+    assert o.counters()["spikes"] > 1000
+    _assert_same_run(g, o, steps)
+    g.close()
+
+
+def test_run_4x4_swa_full_second(snn, oracle_mod):
+    """The 4x4 SWA workload over its full 1 s (10,000 steps)."""
+    wl = W.grid_4x4_swa()
+    g = snn.Network(wl["params"], wl["seed"])
+    g.run(wl["steps"])
+    o = _oracle(oracle_mod, wl["params"], wl["seed"], wl["steps"])
+    _assert_same_run(g, o, wl["steps"])
+    g.close()
+
+
+@pytest.mark.parametrize("grid,regime", [((1, 1), "AW"), ((3, 2), "AW"), ((2, 3), "SWA")])
+def test_run_small_grids(snn, oracle_mod, grid, regime):
+    p = W.base_params(*grid, 1.0, regime)
+    g = snn.Network(p, 5)
+    for n in (1, 7, 50, 443):
+        g.run(n)
+    o = _oracle(oracle_mod, p, 5, 501)
+    _assert_same_run(g, o, 501)
+
+
+def test_run_table_s1_pure_kernel(snn, oracle_mod):
+    """Table S1 three-population efficacies with the pure Eq. 1 kernel."""
+    p = W.table_s1_params(3, 3, 0.6, "AW_8.8Hz")
+    g = snn.Network(p, 3)
+    g.run(800)
+    o = _oracle(oracle_mod, p, 3, 800)
+    _assert_same_run(g, o, 800)
+
+
+def test_run_24x24_window(snn, oracle_mod):
+    """24x24 AW grid at full size: the first 150 steps, both paths."""
+    p = W.base_params(24, 24, 1.0, "AW")
+    o = _oracle(oracle_mod, p, 1, 150)
+    for path in (0, 1):
+        g = snn.Network(p, 1)
+        g.launch = {"path": path}
+        g.run(150)
+        _assert_same_run(g, o, 150)
+        g.close()
+
+
+def test_zero_steps_and_no_spike_input(snn, oracle_mod):
+    p = W.base_params(1, 1, 1.0, "AW")
+    p["nu_ext"] = [0.0, 0.0, 0.0]
+    p["V_th"] = [1000.0, 1000.0, 1000.0]
+    g = snn.Network(p, 9)
+    g.run(0)
+    assert g.stats()["t"] == 0
+    g.run(300)
+    st, ids = g.spikes()
+    assert len(st) == 0 and g.stats()["ext_events"] == 0
+    o = _oracle(oracle_mod, p, 9, 300)
+    _assert_same_run(g, o, 300)
+
+
+# ---------------------------------------------------------------------------
+# batching -- each network identical alone and in the batch
+# ---------------------------------------------------------------------------
+def test_batch_matches_oracle(snn, oracle_mod):
+    specs = [((2, 2), "SWA", W.REC_F32, 11), ((3, 3), "AW", W.REC_I16, 12),
+             ((1, 1), "AW", W.REC_F32, 13), ((2, 3), "SWA", W.REC_I16, 14)]
+    steps = [900, 600, 900, 350]
+    nets, params = [], []
+    for (g2, reg, fmt, seed) in specs:
+        p = W.base_params(*g2, 1.0, reg, record_format=fmt)
+        params.append((p, seed))
+        nets.append(snn.Network(p, seed))
+    snn.run_batch(nets, steps)
+    for (p, seed), n, st in zip(params, nets, steps):
+        o = _oracle(oracle_mod, p, seed, st)
+        _assert_same_run(n, o, st)
+    # a second batch call continues every network from where it stopped
+    snn.run_batch(nets, [100] * 4)
+    for (p, seed), n, st in zip(params, nets, steps):
+        o = _oracle(oracle_mod, p, seed, st + 100)
+        _assert_same_run(n, o, st + 100)
+
+
+# ---------------------------------------------------------------------------
+# launch shapes and the tuner never change results
+# ---------------------------------------------------------------------------
+def test_launch_shapes_and_autotune_keep_results(snn, oracle_mod):
+    p = W.base_params(3, 3, 0.4, "SWA")
+    o = _oracle(oracle_mod, p, 21, 700)
+    shapes = [dict(path=0, update_block=128, deliver_warps=2, window_steps=33, deliver_chunk=8),
+              dict(path=0, update_block=512, deliver_warps=8, window_steps=700, deliver_chunk=1152),
+              dict(path=0, update_block=256, deliver_warps=1, window_steps=50, deliver_chunk=200),
+              dict(path=1, fused_block=128, fused_items_per_sm=1, window_steps=64, deliver_chunk=576),
+              dict(path=1, fused_block=512, fused_items_per_sm=4, window_steps=128, deliver_chunk=96)]
+    for sh in shapes:
+        g = snn.Network(p, 21)
+        g.launch = sh
+        g.run(700)
+        _assert_same_run(g, o, 700)
+        g.close()
+    g = snn.Network(p, 21)
+    g.run(200)
+    g.autotune(50)
+    g.run(500)
+    _assert_same_run(g, o, 700)
+
+
+# ---------------------------------------------------------------------------
+# bounded waits: a wait that gives up is reported, the context stays usable
+# ---------------------------------------------------------------------------
+def test_wait_limit_zero_reports_timeout(snn):
+    p = W.base_params(2, 2, 1.0, "AW")
+    for path in (0, 1):
+        g = snn.Network(p, 4)
+        g.launch = {"path": path}
+        g.set_wait_limit(0)
+        with pytest.raises(snn.SnnError) as ei:
+            g.run(200)
+        assert ei.value.code == -4
+        g.close()
+    # the device is still healthy: a fresh network runs normally
+    g = snn.Network(p, 4)
+    g.run(50)
+    assert g.stats()["t"] == 50
