@@ -91,6 +91,9 @@ typedef struct snn_stats {
   uint64_t device_bytes;   /* device memory held by the network */
   uint64_t record_bytes;   /* of which synapse records */
   double build_ms;         /* wall time of snn_build_network */
+  uint64_t h2d_bytes;      /* host-to-device bytes copied by the library for this network */
+  uint64_t d2h_bytes;      /* device-to-host bytes copied by the library for this network */
+  uint64_t kernel_launches;/* kernels launched on this network's behalf (graph nodes included) */
 } snn_stats;
 
 /* Launch shapes; chosen by snn_autotune or set explicitly. */
@@ -103,6 +106,8 @@ typedef struct snn_launch {
   int32_t window_steps;    /* steps per captured CUDA graph (1..4096) */
   int32_t deliver_chunk;   /* synapse records per delivery work item, multiple of 8
                               (two-kernel path <= 1152, fused path <= 576) */
+  int32_t update_groups;   /* groups of 4 neurons per update thread: 1, 2 or 4
+                              (512-thread blocks: 1 or 2) */
 } snn_launch;
 
 typedef void *(*snn_alloc_fn)(size_t bytes, void *ctx);
@@ -170,6 +175,13 @@ int snn_set_launch(snn_handle h, const snn_launch *cfg);
  * and keep the fastest; the network's state, counters and records are
  * restored afterwards, so results are unchanged. */
 int snn_autotune(snn_handle h, uint32_t trial_steps);
+
+/* Advance the network by `steps` steps with the two-kernel path launched
+ * directly (no graph), bracketing every launch with CUDA events on the
+ * network's stream.  ms_out[0] / ms_out[1] receive the mean duration of one
+ * update / one delivery launch in milliseconds.  Results are identical to
+ * snn_run; the call exists to measure kernels without a profiler. */
+int snn_time_kernels(snn_handle h, uint32_t steps, double *ms_out);
 
 /* Release the network and its device memory. */
 void snn_free(snn_handle h);

@@ -110,6 +110,8 @@ def _load():
     lib.orc_trace.argtypes = [vp, vp, vp]
     lib.orc_neuron_trace.argtypes = [P(Params), i32, ctypes.c_float, ctypes.c_float, u32, vp, vp, vp, vp]
     lib.orc_philox4x32_10.argtypes = [vp, u32, u32, vp]
+    lib.orc_row_build_seconds.restype = ctypes.c_double
+    lib.orc_row_build_seconds.argtypes = [vp]
     lib.orc_inv_phi.restype = ctypes.c_double
     lib.orc_inv_phi.argtypes = [ctypes.c_double]
     _lib = lib
@@ -202,6 +204,10 @@ class OracleNet:
         out = np.zeros((self.D, self.N), np.int32)
         self._lib.orc_ring(self._h, _ptr(out))
         return out
+
+    def row_build_seconds(self) -> float:
+        """Wall time the oracle spent generating rows on first use."""
+        return self._lib.orc_row_build_seconds(self._h)
 
     def counters(self) -> dict:
         out = np.zeros(3, np.uint64)

@@ -28,9 +28,11 @@
  * Step contract (time-driven, dt = 0.1 ms, D = n_delay + 1 ring slots):
  *   for each neuron n (population p) at step t, slot st = t mod D:
  *     I = ring[st][n]; ring[st][n] = 0
- *     (r0..r3) = Philox4x32-10(key = seed, ctr = (n, t, 1, 0))
- *     k_ext = #{k < 16 : r0 >= T_p[k]}  (Poisson CDF thresholds)
- *     I += amp_p[z-index of external event e] for e < k_ext
+ *     w = word (n mod 4) of Philox4x32-10(key = seed, ctr = (n div 4, t, 1, 0))
+ *     k_ext = #{k < 16 : (w >> 12) >= T_p[k]}  (Poisson CDF thresholds, 2^20 scale)
+ *     I += amp_p[z-index of external event e] for e < k_ext: event 0 takes
+ *          w & 0xFFF, event e >= 1 the top 12 bits of 16-bit half (e-1) mod 8
+ *          of Philox(key = seed, ctr = (n, t, 3, (e-1) div 8))
  *     if ref > 0: ref -= 1, V = V_r                      (input discarded)
  *     else: V = fl(fl(E + fl(fl(P_VV*fl(V-E)) + fl(P_Vc*c))) + fl(I*2^-16))
  *           if V > V_theta: spike, V = V_r, ref = n_arp
@@ -42,6 +44,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
 
 #define ORC_K 1250
 #define ORC_ZTAB 4096
@@ -93,6 +96,7 @@ typedef struct {
   uint32_t *rates;          /* [bin][G][3] */
   size_t rates_bins;
   uint64_t n_spikes, n_ext_events, n_rec_events;
+  double row_build_seconds;   /* wall time spent generating rows on first use */
   /* optional per-step input trace for tiny tests: recurrent and external input */
   int32_t *trace_rec, *trace_ext;
   uint32_t trace_t0, trace_steps;
@@ -177,7 +181,7 @@ static void orc_build_pop(orc_net *net, int p) {
   double pmf = exp(-lam), cum = pmf;
   for (int k = 0; k < ORC_KMAX; ++k) {
     if (k > 0) { pmf = (pmf * lam) / (double)k; cum = cum + pmf; }
-    q->thr[k] = (uint64_t)floor(cum * 4294967296.0);
+    q->thr[k] = (uint64_t)floor(cum * 1048576.0);
   }
   /* external amplitude table: J_ext + sigma*z in 2^-16 mV */
   float sig = P->dJ_ext_frac * fabsf(P->J_ext[p]);
@@ -273,12 +277,22 @@ void orc_build_row(const orc_net *net, uint32_t s, uint32_t *key_out, float *w_o
   free(start); free(w); free(k);
 }
 
+static double orc_now(void) {
+  struct timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
+
 static void orc_ensure_row(orc_net *net, uint32_t s) {
   if (net->row_key[s]) return;
+  double t_in = orc_now();
   net->row_key[s] = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)net->M);
   net->row_w[s] = (float *)malloc(sizeof(float) * (size_t)net->M);
   orc_build_row(net, s, net->row_key[s], net->row_w[s]);
+  net->row_build_seconds += orc_now() - t_in;
 }
+
+double orc_row_build_seconds(const orc_net *net) { return net->row_build_seconds; }
 
 /* Fixed-point weight (2^-16 mV) delivered by one record. */
 static int32_t orc_wfix(const orc_net *net, float w) {
@@ -317,21 +331,16 @@ int orc_neuron_update(const orc_pop *q, float *V, float *c, int32_t *ref, int32_
   return spike;
 }
 
-/* 16-bit half number e of the external-amplitude stream of (n, t). */
-static uint32_t orc_ext_half(const orc_net *net, const uint32_t r[4], uint32_t n, uint32_t t, int32_t e) {
-  uint32_t word;
-  int32_t h;
-  if (e < 6) {
-    word = r[1 + e / 2];
-    h = e & 1;
-  } else {
-    uint32_t w4[4];
-    int32_t ee = e - 6;
-    orc_rng(net, n, t, 1u, (uint32_t)(1 + ee / 8), w4);
-    word = w4[(ee % 8) / 2];
-    h = ee & 1;
-  }
-  return h ? (word >> 16) : (word & 0xFFFFu);
+/* Gaussian-table index (12 bits) of external event e of neuron n at step t;
+ * `w` is the neuron's 32-bit word of the step's shared draw. */
+static uint32_t orc_ext_index(const orc_net *net, uint32_t w, uint32_t n, uint32_t t, int32_t e) {
+  if (e == 0) return w & 0xFFFu;
+  uint32_t r[4];
+  int32_t i = (e - 1) % 8;
+  orc_rng(net, n, t, 3u, (uint32_t)((e - 1) / 8), r);
+  uint32_t word = r[i / 2];
+  uint32_t half = (i & 1) ? (word >> 16) : (word & 0xFFFFu);
+  return half >> 4;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -419,11 +428,12 @@ int orc_run(orc_net *net, uint32_t steps) {
       int32_t I = slot[n];
       slot[n] = 0;
       uint32_t r[4];
-      orc_rng(net, (uint32_t)n, t, 1u, 0u, r);
+      orc_rng(net, (uint32_t)n / 4u, t, 1u, 0u, r);
+      uint32_t w = r[n % 4];
       int32_t kext = 0;
-      while (kext < ORC_KMAX && (uint64_t)r[0] >= q->thr[kext]) kext++;
+      while (kext < ORC_KMAX && (uint64_t)(w >> 12) >= q->thr[kext]) kext++;
       int32_t Iext = 0;
-      for (int32_t e = 0; e < kext; ++e) Iext += q->amp[orc_ext_half(net, r, (uint32_t)n, t, e) >> 4];
+      for (int32_t e = 0; e < kext; ++e) Iext += q->amp[orc_ext_index(net, w, (uint32_t)n, t, e)];
       net->n_ext_events += (uint64_t)kext;
       if (tracing) {
         size_t o = (size_t)(t - net->trace_t0) * (size_t)N + (size_t)n;

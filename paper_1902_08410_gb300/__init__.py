@@ -212,6 +212,13 @@ class Network:
         _check(self._lib.snn_autotune(self._h, int(trial_steps)))
         return self.launch
 
+    def time_kernels(self, steps: int) -> dict:
+        """Mean per-launch durations (ms) of the update and delivery kernels over
+        `steps` directly launched steps, measured with CUDA events."""
+        out = (ctypes.c_double * 2)()
+        _check(self._lib.snn_time_kernels(self._h, int(steps), out))
+        return {"update_ms": out[0], "deliver_ms": out[1]}
+
     def set_wait_limit(self, iterations: int) -> None:
         _check(self._lib.snn_debug_set_wait_limit(self._h, int(iterations)))
 

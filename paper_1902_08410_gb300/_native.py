@@ -87,13 +87,15 @@ class SnnParams(ctypes.Structure):
 class SnnStats(ctypes.Structure):
     _fields_ = [("t", ctypes.c_uint64), ("spikes", ctypes.c_uint64), ("rec_events", ctypes.c_uint64),
                 ("ext_events", ctypes.c_uint64), ("n_neurons", ctypes.c_uint64), ("n_synapses", ctypes.c_uint64),
-                ("device_bytes", ctypes.c_uint64), ("record_bytes", ctypes.c_uint64), ("build_ms", ctypes.c_double)]
+                ("device_bytes", ctypes.c_uint64), ("record_bytes", ctypes.c_uint64), ("build_ms", ctypes.c_double),
+                ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64)]
 
 
 class SnnLaunch(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("update_block", ctypes.c_int32), ("deliver_warps", ctypes.c_int32),
                 ("fused_block", ctypes.c_int32), ("fused_items_per_sm", ctypes.c_int32),
-                ("window_steps", ctypes.c_int32), ("deliver_chunk", ctypes.c_int32)]
+                ("window_steps", ctypes.c_int32), ("deliver_chunk", ctypes.c_int32),
+                ("update_groups", ctypes.c_int32)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -103,7 +105,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 EXPORTS = ["snn_set_allocator", "snn_footprint", "snn_build_network", "snn_run", "snn_run_batch",
            "snn_read_spikes", "snn_rates", "snn_read_state", "snn_read_row", "snn_get_stats",
            "snn_get_launch", "snn_set_launch", "snn_autotune", "snn_free", "snn_last_error",
-           "snn_debug_set_wait_limit"]
+           "snn_debug_set_wait_limit", "snn_time_kernels"]
 
 _lib = None
 
@@ -137,6 +139,7 @@ def load(build_if_needed: bool = True):
         "snn_free": ([vp], None),
         "snn_last_error": ([], ctypes.c_char_p),
         "snn_debug_set_wait_limit": ([vp, u32], ctypes.c_int),
+        "snn_time_kernels": ([vp, u32, P(ctypes.c_double)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)

@@ -161,7 +161,7 @@ PopTables pop_tables(const snn_params &p, int q) {
       pk = (pk * lam) / (double)k;
       acc = acc + pk;
     }
-    t.thr[k] = (unsigned long long)std::floor(acc * 4294967296.0);
+    t.thr[k] = (unsigned long long)std::floor(acc * 1048576.0);   // compared with a 20-bit uniform
   }
   return t;
 }
@@ -320,6 +320,7 @@ struct snn_net {
   double build_ms = 0.0;
   bool broken = false;
   int sm_count = 0;
+  uint64_t h2d = 0, d2h = 0, launches = 0;
 };
 
 static int sm_count_cached() {
@@ -336,6 +337,7 @@ static void default_launch(snn_net *h) {
   h->cfg.fused_items_per_sm = 2;
   h->cfg.window_steps = (int32_t)h->L.window;
   h->cfg.deliver_chunk = 384;
+  h->cfg.update_groups = 2;
 }
 
 extern "C" int snn_footprint(const snn_params *p, size_t *bytes_out) {
@@ -476,6 +478,8 @@ extern "C" int snn_build_network(const snn_params *p, uint64_t seed, void *cuda_
   if (!cdf.empty()) CU_TRY(cudaMemcpyAsync(d_cdf, cdf.data(), cdf.size() * 4, cudaMemcpyHostToDevice, s));
   CU_TRY(cudaMemcpyAsync(d_z, ztab.data(), kZTab * 4, cudaMemcpyHostToDevice, s));
   CU_TRY(cudaMemcpyAsync(base + L.off_amp, amp.data(), amp.size() * 4, cudaMemcpyHostToDevice, s));
+  h->h2d += cdf.size() * 4 + kZTab * 4 + amp.size() * 4;
+  h->launches += 2;
   bd.cdf = d_cdf;
   bd.ztab = d_z;
   CU_TRY(cudaMemsetAsync(base + L.off_ring, 0, (size_t)L.D * L.N_pad * 4, s));
@@ -509,7 +513,7 @@ static int capture_window(snn_net *h, uint32_t window) {
   cudaError_t err = cudaSuccess;
   const int sms = h->sm_count > 0 ? h->sm_count : 148;
   for (uint32_t k = 0; k < window && err == cudaSuccess; ++k) {
-    err = launch_update(h->hd, k, c.update_block, cs);
+    err = launch_update(h->hd, k, c.update_block, c.update_groups, cs);
     if (err == cudaSuccess) err = launch_deliver(h->hd, k, (uint32_t)c.deliver_chunk, c.deliver_warps, sms * 4, cs);
   }
   cudaGraph_t g = nullptr;
@@ -535,6 +539,7 @@ static int drain_window(snn_net *h, uint64_t t0, cudaStream_t s) {
   const size_t rec_bytes = L.off_entries - L.off_rec;
   CU_TRY(cudaMemcpyAsync(h->pinned_rec, base + L.off_rec, rec_bytes, cudaMemcpyDeviceToHost, s));
   CU_TRY(cudaStreamSynchronize(s));
+  h->d2h += rec_bytes;
   const RecHeader *rh = reinterpret_cast<const RecHeader *>(h->pinned_rec);
   if (rh->status & kStatusTimeout) {
     h->broken = true;
@@ -559,6 +564,7 @@ static int drain_window(snn_net *h, uint64_t t0, cudaStream_t s) {
     }
     CU_TRY(cudaMemcpyAsync(h->pinned_entries, base + L.off_entries, (size_t)n_rec * 8, cudaMemcpyDeviceToHost, s));
     CU_TRY(cudaStreamSynchronize(s));
+    h->d2h += (uint64_t)n_rec * 8;
     const size_t old = h->raster.size();
     h->raster.resize(old + n_rec);
     for (uint32_t i = 0; i < n_rec; ++i) {
@@ -593,6 +599,8 @@ static int run_plain(snn_net *h, uint64_t steps) {
     h->pinned_win->bin0 = (uint32_t)(t0 / (uint64_t)h->p.bin_steps);
     CU_TRY(cudaMemcpyAsync(base + h->L.off_win, h->pinned_win, sizeof(NetWin), cudaMemcpyHostToDevice, h->stream));
     CU_TRY(cudaGraphLaunch(h->exec, h->stream));
+    h->h2d += sizeof(NetWin);
+    h->launches += 2ull * window;
     rc = drain_window(h, t0, h->stream);
     if (rc) return rc;
     h->t = t0 + n;
@@ -730,6 +738,8 @@ static int run_fused(snn_net *const *hs, const uint64_t *steps, int32_t n) {
     }
     CU_TRY(cudaMemcpyAsync(B.wins.p, B.pinned_wins, (size_t)n * sizeof(NetWin), cudaMemcpyHostToDevice, s));
     CU_TRY(cudaGraphLaunch(B.exec, s));
+    hs[0]->launches += window;   // one fused kernel per step for the whole batch
+    for (int i = 0; i < n; ++i) hs[i]->h2d += sizeof(NetWin) + sizeof(NetDev);
     for (int i = 0; i < n; ++i) {
       snn_net *h = hs[i];
       const uint64_t adv = std::min<uint64_t>(window, left[i]);
@@ -855,6 +865,57 @@ extern "C" int snn_get_stats(snn_handle h, snn_stats *out) {
   out->device_bytes = h->arena.bytes;
   out->record_bytes = (uint64_t)h->L.N * h->L.row_bytes;
   out->build_ms = h->build_ms;
+  out->h2d_bytes = h->h2d;
+  out->d2h_bytes = h->d2h;
+  out->kernel_launches = h->launches;
+  return SNN_OK;
+}
+
+extern "C" int snn_time_kernels(snn_handle h, uint32_t steps, double *ms_out) {
+  if (!h || !ms_out) return fail(SNN_ERR_ARG, "null argument");
+  if (h->broken) return fail(SNN_ERR_STATE, "network is invalid after an earlier failure");
+  if (steps == 0 || steps > h->L.window) return fail(SNN_ERR_ARG, "steps must be in 1..window");
+  const uint64_t t0 = h->t;
+  if (t0 + steps > 0xFFFFFFFFull) return fail(SNN_ERR_LIMIT, "step counter beyond 2^32");
+  uint8_t *base = static_cast<uint8_t *>(h->arena.p);
+  cudaStream_t s = h->stream;
+  h->hd.wait_limit = h->wait_limit;
+  h->pinned_win->t0 = (uint32_t)t0;
+  h->pinned_win->t_end = (uint32_t)(t0 + steps);
+  h->pinned_win->bin0 = (uint32_t)(t0 / (uint64_t)h->p.bin_steps);
+  CU_TRY(cudaMemcpyAsync(base + h->L.off_win, h->pinned_win, sizeof(NetWin), cudaMemcpyHostToDevice, s));
+  std::vector<cudaEvent_t> ev(4 * (size_t)steps, nullptr);
+  for (auto &e : ev) CU_TRY(cudaEventCreate(&e));
+  struct EvGuard {
+    std::vector<cudaEvent_t> *v;
+    ~EvGuard() {
+      for (auto e : *v)
+        if (e) cudaEventDestroy(e);
+    }
+  } evg{&ev};
+  const int sms = h->sm_count > 0 ? h->sm_count : 148;
+  for (uint32_t k = 0; k < steps; ++k) {
+    CU_TRY(cudaEventRecord(ev[4 * k + 0], s));
+    CU_TRY(launch_update(h->hd, k, h->cfg.update_block, h->cfg.update_groups, s));
+    CU_TRY(cudaEventRecord(ev[4 * k + 1], s));
+    CU_TRY(cudaEventRecord(ev[4 * k + 2], s));
+    CU_TRY(launch_deliver(h->hd, k, (uint32_t)h->cfg.deliver_chunk, h->cfg.deliver_warps, sms * 4, s));
+    CU_TRY(cudaEventRecord(ev[4 * k + 3], s));
+  }
+  h->launches += 2ull * steps;
+  int rc = drain_window(h, t0, s);
+  if (rc) return rc;
+  h->t = t0 + steps;
+  double up = 0, dl = 0;
+  for (uint32_t k = 0; k < steps; ++k) {
+    float a = 0, b = 0;
+    CU_TRY(cudaEventElapsedTime(&a, ev[4 * k + 0], ev[4 * k + 1]));
+    CU_TRY(cudaEventElapsedTime(&b, ev[4 * k + 2], ev[4 * k + 3]));
+    up += a;
+    dl += b;
+  }
+  ms_out[0] = up / steps;
+  ms_out[1] = dl / steps;
   return SNN_OK;
 }
 
@@ -877,6 +938,10 @@ extern "C" int snn_set_launch(snn_handle h, const snn_launch *cfg) {
   if (c.window_steps < 1 || c.window_steps > 4096) return fail(SNN_ERR_ARG, "window_steps in 1..4096");
   if (c.deliver_chunk < 8 || c.deliver_chunk % 8 || (uint32_t)c.deliver_chunk > max_chunk_records())
     return fail(SNN_ERR_ARG, "deliver_chunk must be a multiple of 8 in 8..1152");
+  if (c.update_groups != 1 && c.update_groups != 2 && c.update_groups != 4)
+    return fail(SNN_ERR_ARG, "update_groups must be 1, 2 or 4");
+  if (c.update_block == 512 && c.update_groups == 4)
+    return fail(SNN_ERR_ARG, "update_groups 4 needs update_block <= 256");
   h->cfg = c;
   return SNN_OK;
 }
@@ -918,16 +983,18 @@ extern "C" int snn_autotune(snn_handle h, uint32_t trial_steps) {
   const snn_launch orig = h->cfg;
 
   std::vector<snn_launch> cands;
-  for (int ub : {128, 256, 512})
-    for (int dw : {2, 4, 8})
-      for (int ch : {1152, 576, 384, 192}) {
-        snn_launch c = orig;
-        c.path = 0;
-        c.update_block = ub;
-        c.deliver_warps = dw;
-        c.deliver_chunk = ch;
-        cands.push_back(c);
-      }
+  for (int ub : {128, 256})
+    for (int ug : {1, 2, 4})
+      for (int dw : {2, 4})
+        for (int ch : {1152, 576, 384}) {
+          snn_launch c = orig;
+          c.path = 0;
+          c.update_block = ub;
+          c.update_groups = ug;
+          c.deliver_warps = dw;
+          c.deliver_chunk = ch;
+          cands.push_back(c);
+        }
   for (int fb : {128, 256, 512})
     for (int ips : {1, 2, 4})
       for (int ch : {576, 288, 144}) {

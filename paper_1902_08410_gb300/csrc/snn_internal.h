@@ -102,7 +102,7 @@ struct FusedTable {
 cudaError_t prepare_kernels();
 cudaError_t launch_build_rows(const NetDev &h_nd, const BuildDev &bd, cudaStream_t s);
 cudaError_t launch_init_state(const NetDev &nd, cudaStream_t s);
-cudaError_t launch_update(const NetDev &nd, uint32_t k, int block, cudaStream_t s);
+cudaError_t launch_update(const NetDev &nd, uint32_t k, int block, int groups, cudaStream_t s);
 cudaError_t launch_deliver(const NetDev &nd, uint32_t k, uint32_t chunk, int warps, int blocks, cudaStream_t s);
 cudaError_t launch_fused(const FusedTable &tab, uint32_t k, int block, int blocks, cudaStream_t s);
 uint32_t max_chunk_records();        // largest chunk of the two-kernel delivery

@@ -5,15 +5,16 @@
 // -fmad=false):
 //   Eq. 2 over one step for neuron n at step t (slot st = t mod D):
 //     I  = ring[st][n]; ring[st][n] = 0
-//     r  = Philox4x32-10(key = seed, ctr = (n, t, 1, 0))
-//     k  = #{j < 16 : r.x >= thr[pop][j]}           (Poisson count, Sec. 2.1)
-//     I += amp[pop][half_e >> 4] for the k external events
+//     w  = word (n mod 4) of Philox4x32-10(key = seed, ctr = (n div 4, t, 1, 0))
+//     k  = #{j < 16 : (w >> 12) >= thr[pop][j]}     (Poisson count, Sec. 2.1)
+//     I += amp[pop][z_e] for the k external events: z_0 = w & 0xFFF, z_e (e >= 1)
+//          = top 12 bits of half (e-1) mod 8 of Philox(seed, (n, t, 3, (e-1) div 8))
 //     ref > 0 : ref -= 1, V = V_r                    (refractory clamp, Sec. 2.2)
 //     else    : V = (E + (P_VV*(V-E) + P_Vc*c)) + I*2^-16; spike if V > V_th
 //     c = P_cc*c (+ alpha when the neuron fired)
 //   Delivery of a spike of step t: every record (d, target, w) of the source's
-//   row adds its fixed-point weight to ring[(t+d) mod D][target] (int32 atomics,
-//   so the sum does not depend on order).
+//   row adds its fixed-point weight to ring[(t+d) mod D][target] (int32
+//   reductions, so the sum does not depend on order).
 #include <algorithm>
 #include <cstdint>
 
@@ -110,37 +111,55 @@ __device__ __forceinline__ void red_add_u32(uint32_t *addr, uint32_t v) {
   asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(addr), "r"(v) : "memory");
 }
 
+// Loads that bypass L1 (streamed state), keeping L1 for the amplitude table.
+__device__ __forceinline__ float4 ld_na_f4(const float4 *p) {
+  float4 v;
+  asm volatile("ld.global.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+__device__ __forceinline__ int4 ld_na_i4(const int4 *p) {
+  int4 v;
+  asm volatile("ld.global.L1::no_allocate.v4.s32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_na_u32(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.global.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+
 // ---------------------------------------------------------------------------
 // Neuron update (Eq. 2 over one step, Poisson drive) of 4 consecutive neurons.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t poisson_count(const NetDev &nd, int pop, uint32_t u) {
+__device__ __forceinline__ uint32_t poisson_count(const NetDev &nd, int pop, uint32_t w) {
+  const unsigned long long u = w >> 12;   // 20-bit uniform
   uint32_t k = 0;
-  while (k < (uint32_t)kPoisMax && (unsigned long long)u >= nd.thr[pop][k]) ++k;
+  while (k < (uint32_t)kPoisMax && u >= nd.thr[pop][k]) ++k;
   return k;
 }
 
-// Sum of the amplitudes of k external events of neuron n at step t (2^-16 mV).
-__device__ __noinline__ int32_t external_amplitudes(const NetDev &nd, int pop, const uint4 r, uint32_t k, uint32_t n,
-                                                    uint32_t t) {
+// Amplitudes of external events 1..k-1 of neuron n at step t (2^-16 mV); rare.
+__device__ __noinline__ int32_t extra_amplitudes(const NetDev &nd, int pop, uint32_t k, uint32_t n, uint32_t t) {
   const int32_t *ap = nd.amp + pop * kZTab;
   int32_t I = 0;
-  for (uint32_t e = 0; e < k; ++e) {
-    uint32_t word, hi;
-    if (e < 6u) {
-      const uint32_t w = e >> 1;
-      word = (w == 0) ? r.y : ((w == 1) ? r.z : r.w);
-      hi = e & 1u;
-    } else {
-      const uint32_t ee = e - 6u;
-      const uint4 q = philox4x32_10(n, t, 1u, 1u + ee / 8u, nd.key0, nd.key1);
-      const uint32_t w = (ee % 8u) >> 1;
-      word = (w == 0) ? q.x : ((w == 1) ? q.y : ((w == 2) ? q.z : q.w));
-      hi = ee & 1u;
-    }
-    const uint32_t half = hi ? (word >> 16) : (word & 0xFFFFu);
+  uint4 q = make_uint4(0, 0, 0, 0);
+  for (uint32_t e = 1; e < k; ++e) {
+    const uint32_t i = (e - 1u) & 7u;
+    if (i == 0) q = philox4x32_10(n, t, 3u, (e - 1u) >> 3, nd.key0, nd.key1);
+    const uint32_t w = i >> 1;
+    const uint32_t word = (w == 0) ? q.x : ((w == 1) ? q.y : ((w == 2) ? q.z : q.w));
+    const uint32_t half = (i & 1u) ? (word >> 16) : (word & 0xFFFFu);
     I += __ldg(ap + (half >> 4));
   }
   return I;
+}
+
+__device__ __forceinline__ void red_add_u64(unsigned long long *addr, unsigned long long v) {
+  asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(addr), "l"(v) : "memory");
 }
 
 __device__ __forceinline__ bool neuron_step(const NetDev &nd, int pop, float &V, float &c, uint32_t &ref, int32_t I) {
@@ -171,38 +190,51 @@ __device__ __forceinline__ bool neuron_step(const NetDev &nd, int pop, float &V,
   return spike;
 }
 
-// Update neurons n0..n0+3 (n0 % 4 == 0, n0 < N_pad) at step t; returns the
-// 4-bit spike mask and adds the number of external events to n_ext.
-__device__ __forceinline__ uint32_t update4(const NetDev &nd, uint32_t n0, uint32_t t, uint32_t &n_ext) {
+// State of 4 consecutive neurons n0..n0+3 (n0 % 4 == 0, n0 < N_pad).
+struct Group4 {
+  float4 V, c;
+  uint32_t ref;   // 4 x u8
+  int4 I;         // ring slot t
+};
+
+__device__ __forceinline__ void load_state4(const NetDev &nd, uint32_t n0, Group4 &g) {
   const uint32_t i4 = n0 >> 2;
-  const uint32_t st = t % nd.D;
-  const float4 V4 = reinterpret_cast<const float4 *>(nd.V)[i4];
-  const float4 c4 = reinterpret_cast<const float4 *>(nd.c)[i4];
-  const uchar4 r4 = reinterpret_cast<const uchar4 *>(nd.ref)[i4];
-  int4 *slot = reinterpret_cast<int4 *>(nd.ring + (size_t)st * nd.N_pad);
-  const int4 I4 = slot[i4];
-  slot[i4] = make_int4(0, 0, 0, 0);
-  // the four counter-based draws are independent: issue them together
-  uint4 R[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) R[q] = philox4x32_10(n0 + q, t, 1u, 0u, nd.key0, nd.key1);
+  g.V = ld_na_f4(reinterpret_cast<const float4 *>(nd.V) + i4);
+  g.c = ld_na_f4(reinterpret_cast<const float4 *>(nd.c) + i4);
+  g.ref = ld_na_u32(reinterpret_cast<const uint32_t *>(nd.ref) + i4);
+}
+
+__device__ __forceinline__ void load_ring4(const NetDev &nd, uint32_t n0, uint32_t st, Group4 &g) {
+  int4 *slot = reinterpret_cast<int4 *>(nd.ring + (size_t)st * nd.N_pad) + (n0 >> 2);
+  g.I = ld_na_i4(slot);
+  *slot = make_int4(0, 0, 0, 0);
+}
+
+// Advance the 4 neurons of g by step t; returns the 4-bit spike mask and adds
+// the number of external events to n_ext.
+__device__ __forceinline__ uint32_t step4(const NetDev &nd, uint32_t n0, uint32_t t, Group4 &g, uint32_t &n_ext) {
+  // one counter-based draw serves the four neurons (word n mod 4 each)
+  const uint4 R = philox4x32_10(n0 >> 2, t, 1u, 0u, nd.key0, nd.key1);
+  const uint32_t Wv[4] = {R.x, R.y, R.z, R.w};
   uint32_t local = n0 % (uint32_t)kK;
   int pops[4];
   uint32_t kx[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     pops[q] = pop_of_local(local);
-    kx[q] = poisson_count(nd, pops[q], R[q].x);
+    kx[q] = poisson_count(nd, pops[q], Wv[q]);
     local = (local + 1u == (uint32_t)kK) ? 0u : local + 1u;
   }
-  int32_t Iv[4] = {I4.x, I4.y, I4.z, I4.w};
+  int32_t Iv[4] = {g.I.x, g.I.y, g.I.z, g.I.w};
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    if (kx[q]) Iv[q] += external_amplitudes(nd, pops[q], R[q], kx[q], n0 + q, t);
-  }
-  float Vv[4] = {V4.x, V4.y, V4.z, V4.w};
-  float cv[4] = {c4.x, c4.y, c4.z, c4.w};
-  uint32_t rv[4] = {r4.x, r4.y, r4.z, r4.w};
+  for (int q = 0; q < 4; ++q)   // first external event: independent table loads
+    if (kx[q]) Iv[q] += __ldg(nd.amp + pops[q] * kZTab + (Wv[q] & 0xFFFu));
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (kx[q] > 1u) Iv[q] += extra_amplitudes(nd, pops[q], kx[q], n0 + q, t);
+  float Vv[4] = {g.V.x, g.V.y, g.V.z, g.V.w};
+  float cv[4] = {g.c.x, g.c.y, g.c.z, g.c.w};
+  uint32_t rv[4] = {g.ref & 0xFFu, (g.ref >> 8) & 0xFFu, (g.ref >> 16) & 0xFFu, g.ref >> 24};
   uint32_t mask = 0;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -212,36 +244,49 @@ __device__ __forceinline__ uint32_t update4(const NetDev &nd, uint32_t n0, uint3
     }
   }
   if (n0 < nd.N) {
+    const uint32_t i4 = n0 >> 2;
     reinterpret_cast<float4 *>(nd.V)[i4] = make_float4(Vv[0], Vv[1], Vv[2], Vv[3]);
     reinterpret_cast<float4 *>(nd.c)[i4] = make_float4(cv[0], cv[1], cv[2], cv[3]);
-    reinterpret_cast<uchar4 *>(nd.ref)[i4] =
-        make_uchar4((unsigned char)rv[0], (unsigned char)rv[1], (unsigned char)rv[2], (unsigned char)rv[3]);
+    reinterpret_cast<uint32_t *>(nd.ref)[i4] = rv[0] | (rv[1] << 8) | (rv[2] << 16) | (rv[3] << 24);
   }
   return mask;
 }
 
-// Warp-level recording of the warp's spikes (all 32 lanes active; lane L owns
-// neurons n0..n0+3).  Appends raster entries with one returning atomic per
-// warp, counts rates with fire-and-forget reductions, and adds the warp's
-// external events to its own 128-neuron slot.  When `smem_list` is given the
-// ids are also appended there (block-local list for fused delivery).
-__device__ __forceinline__ void record_warp(const NetDev &nd, uint32_t mask, uint32_t n0, uint32_t t, uint32_t k,
-                                            uint32_t bin0, uint32_t n_ext, uint32_t *smem_list,
-                                            uint32_t *smem_count) {
+__device__ __forceinline__ uint32_t update4(const NetDev &nd, uint32_t n0, uint32_t t, uint32_t &n_ext) {
+  Group4 g;
+  load_state4(nd, n0, g);
+  load_ring4(nd, n0, t % nd.D, g);
+  return step4(nd, n0, t, g, n_ext);
+}
+
+// Warp-level recording of the warp's spikes over G groups (all 32 lanes
+// active; in group g lane L owns neurons n0[g]..n0[g]+3, and the warp's 32
+// lanes cover one aligned 128-neuron tile).  Appends raster entries with one
+// returning atomic per warp, counts rates with fire-and-forget reductions and
+// adds each tile's external events to that tile's slot.  When `smem_list` is
+// given the ids are also appended there (block-local list for fused delivery).
+template <int G>
+__device__ __forceinline__ void record_warp(const NetDev &nd, const uint32_t (&mask)[G], const uint32_t (&n0)[G],
+                                            const uint32_t (&n_ext)[G], uint32_t t, uint32_t k, uint32_t bin0,
+                                            uint32_t *smem_list, uint32_t *smem_count) {
   const uint32_t lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
-  uint32_t before = 0, wtot = 0;
+  uint32_t before[G], wtot = 0;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const uint32_t b = __ballot_sync(0xFFFFFFFFu, (mask >> q) & 1u);
-    before += __popc(b & lt);
-    wtot += __popc(b);
+  for (int g = 0; g < G; ++g) {
+    before[g] = wtot;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t b = __ballot_sync(0xFFFFFFFFu, (mask[g] >> q) & 1u);
+      before[g] += __popc(b & lt);
+      wtot += __popc(b);
+    }
+    uint32_t ext = n_ext[g];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ext += __shfl_xor_sync(0xFFFFFFFFu, ext, o);
+    const uint32_t tile = __shfl_sync(0xFFFFFFFFu, n0[g], 0) >> 7;
+    if (lane == 0 && ext) red_add_u64(nd.ext_acc + tile, ext);   // slot owned by this warp
   }
-  uint32_t ext = n_ext;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) ext += __shfl_xor_sync(0xFFFFFFFFu, ext, o);
-  const uint32_t n_first = __shfl_sync(0xFFFFFFFFu, n0, 0);
-  if (lane == 0 && ext) nd.ext_acc[n_first >> 7] += ext;   // slot owned by this warp
   if (wtot == 0) return;
   uint32_t gbase = 0, sbase = 0;
   if (lane == 0) {
@@ -253,16 +298,19 @@ __device__ __forceinline__ void record_warp(const NetDev &nd, uint32_t mask, uin
   if (lane == 0 && gbase + wtot > nd.rec_cap) atomicOr(&nd.rec->status, kStatusRasterOverflow);
   const unsigned long long tag = ((unsigned long long)nd.slot << 48) | ((unsigned long long)k << 32);
   const uint32_t bin = t / nd.bin_steps - bin0;
-  uint32_t pos = before;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    if ((mask >> q) & 1u) {
-      const uint32_t id = n0 + q;
-      if (gbase + pos < nd.rec_cap) nd.rec_entries[gbase + pos] = tag | id;
-      if (smem_list) smem_list[sbase + pos] = id;
-      const uint32_t m = id / (uint32_t)kK;
-      red_add_u32(nd.rates + ((size_t)bin * nd.G + m) * 3u + pop_of_local(id - m * (uint32_t)kK), 1u);
-      ++pos;
+  for (int g = 0; g < G; ++g) {
+    uint32_t pos = before[g];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if ((mask[g] >> q) & 1u) {
+        const uint32_t id = n0[g] + q;
+        if (gbase + pos < nd.rec_cap) nd.rec_entries[gbase + pos] = tag | id;
+        if (smem_list) smem_list[sbase + pos] = id;
+        const uint32_t m = id / (uint32_t)kK;
+        red_add_u32(nd.rates + ((size_t)bin * nd.G + m) * 3u + pop_of_local(id - m * (uint32_t)kK), 1u);
+        ++pos;
+      }
     }
   }
 }
@@ -530,17 +578,53 @@ __global__ void __launch_bounds__(kBuildWarpsMax * 32) k_build_rows(NetDev nd, B
 // Kernel: neuron update + recording (two-kernel path).  No block barrier:
 // spikes are appended per warp.
 // ---------------------------------------------------------------------------
-template <int BLOCK>
+// Each thread advances G groups of 4 neurons; group g of block b covers the
+// neuron range ((b * G + g) * BLOCK + thread) * 4, so every warp owns whole
+// aligned 128-neuron tiles.  The state loads of all groups are issued before
+// the window is read, then the ring slots once the step is known.
+template <int BLOCK, int G>
 __global__ void __launch_bounds__(BLOCK) k_update(const __grid_constant__ NetDev nd, uint32_t k) {
-  const uint32_t n0 = (blockIdx.x * BLOCK + threadIdx.x) * 4u;
-  const uint32_t warp_first = (blockIdx.x * BLOCK + (threadIdx.x & ~31u)) * 4u;
-  if (warp_first >= nd.N_pad) return;   // whole warps: N_pad is a multiple of 128
+  uint32_t n0[G];
+  bool live[G];
+  bool any = false;
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const uint32_t tile0 = ((blockIdx.x * G + g) * BLOCK + (threadIdx.x & ~31u)) * 4u;
+    n0[g] = ((blockIdx.x * G + g) * BLOCK + threadIdx.x) * 4u;
+    live[g] = tile0 < nd.N_pad;     // whole warps: N_pad is a multiple of 128
+    any |= live[g];
+  }
+  if (!any) return;
+  Group4 st4[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g)
+    if (live[g]) load_state4(nd, n0[g], st4[g]);
   const NetWin w = *nd.win;
   const uint32_t t = w.t0 + k;
   if (t >= w.t_end) return;
-  uint32_t n_ext = 0;
-  const uint32_t mask = update4(nd, n0, t, n_ext);
-  record_warp(nd, mask, n0, t, k, w.bin0, n_ext, nullptr, nullptr);
+  const uint32_t slot = t % nd.D;
+#pragma unroll
+  for (int g = 0; g < G; ++g)
+    if (live[g]) load_ring4(nd, n0[g], slot, st4[g]);
+  uint32_t mask[G], n_ext[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    mask[g] = 0;
+    n_ext[g] = 0;
+    if (live[g]) mask[g] = step4(nd, n0[g], t, st4[g], n_ext[g]);
+  }
+  // record per group whose tile is live (warp-uniform)
+  if (live[G - 1]) {
+    record_warp<G>(nd, mask, n0, n_ext, t, k, w.bin0, nullptr, nullptr);
+  } else {
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      if (live[g]) {
+        const uint32_t m1[1] = {mask[g]}, a1[1] = {n0[g]}, e1[1] = {n_ext[g]};
+        record_warp<1>(nd, m1, a1, e1, t, k, w.bin0, nullptr, nullptr);
+      }
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -550,11 +634,12 @@ __global__ void __launch_bounds__(BLOCK) k_update(const __grid_constant__ NetDev
 __global__ void __launch_bounds__(256) k_deliver(const __grid_constant__ NetDev nd, uint32_t k, uint32_t chunk) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint64_t s_bars[16];
+  const RecHeader rh = *nd.rec;   // issued together with the window load
   const NetWin w = *nd.win;
   const uint32_t t = w.t0 + k;
   if (t >= w.t_end) return;
-  const uint32_t cur = min(nd.rec->cursor, nd.rec_cap);
-  const uint32_t base = nd.rec->step_base[t & 1u];
+  const uint32_t cur = min(rh.cursor, nd.rec_cap);
+  const uint32_t base = rh.step_base[t & 1u];
   if (blockIdx.x == 0 && threadIdx.x == 0) nd.rec->step_base[(t + 1u) & 1u] = cur;
   const uint32_t count = cur > base ? cur - base : 0u;
   const uint32_t nch = (nd.M_pad + chunk - 1u) / chunk;
@@ -605,9 +690,10 @@ __global__ void __launch_bounds__(512) k_fused(const __grid_constant__ FusedTabl
     const uint32_t n0 = item.n_begin + threadIdx.x * 4u;
     const uint32_t warp_first = item.n_begin + warp * 128u;
     if (warp_first < nd.N_pad) {
-      uint32_t n_ext = 0;
-      const uint32_t mask = update4(nd, n0, t, n_ext);
-      record_warp(nd, mask, n0, t, k, w.bin0, n_ext, s_ids, &s_count);
+      uint32_t n_ext[1] = {0};
+      const uint32_t mask[1] = {update4(nd, n0, t, n_ext[0])};
+      const uint32_t a1[1] = {n0};
+      record_warp<1>(nd, mask, a1, n_ext, t, k, w.bin0, s_ids, &s_count);
     }
     __syncthreads();
     const uint32_t cnt = s_count;
@@ -660,16 +746,16 @@ cudaError_t launch_build_rows(const NetDev &h_nd, const BuildDev &bd, cudaStream
   return cudaGetLastError();
 }
 
-cudaError_t launch_update(const NetDev &nd, uint32_t k, int block, cudaStream_t s) {
-  const uint32_t threads_needed = nd.N_pad / 4u;
-  const uint32_t blocks = (threads_needed + block - 1) / block;
-  switch (block) {
-    case 128: k_update<128><<<blocks, 128, 0, s>>>(nd, k); break;
-    case 256: k_update<256><<<blocks, 256, 0, s>>>(nd, k); break;
-    case 512: k_update<512><<<blocks, 512, 0, s>>>(nd, k); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+cudaError_t launch_update(const NetDev &nd, uint32_t k, int block, int groups, cudaStream_t s) {
+  const uint32_t per_block = (uint32_t)block * 4u * (uint32_t)groups;
+  const uint32_t blocks = (nd.N_pad + per_block - 1) / per_block;
+#define SNN_UPD(B, G) \
+  if (block == B && groups == G) { k_update<B, G><<<blocks, B, 0, s>>>(nd, k); return cudaGetLastError(); }
+  SNN_UPD(128, 1) SNN_UPD(128, 2) SNN_UPD(128, 4)
+  SNN_UPD(256, 1) SNN_UPD(256, 2) SNN_UPD(256, 4)
+  SNN_UPD(512, 1) SNN_UPD(512, 2)
+#undef SNN_UPD
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_deliver(const NetDev &nd, uint32_t k, uint32_t chunk, int warps, int blocks, cudaStream_t s) {
