@@ -102,10 +102,10 @@ typedef struct snn_launch {
   int32_t update_block;    /* threads per update block: 128, 256 or 512 */
   int32_t deliver_warps;   /* warps per deliver block: 1..8 */
   int32_t fused_block;     /* threads per fused-step block: 128..512 */
-  int32_t fused_items_per_sm; /* resident fused blocks per SM to launch (1..8) */
+  int32_t fused_items_per_sm; /* fused blocks per SM to launch (1..32, capped by occupancy) */
   int32_t window_steps;    /* steps per captured CUDA graph (1..4096) */
   int32_t deliver_chunk;   /* synapse records per delivery work item, multiple of 8
-                              (two-kernel path <= 1152, fused path <= 576) */
+                              (two-kernel path <= 1152, fused path <= 256) */
   int32_t update_groups;   /* groups of 4 neurons per update thread: 1, 2 or 4
                               (512-thread blocks: 1 or 2) */
 } snn_launch;

@@ -333,8 +333,8 @@ static void default_launch(snn_net *h) {
   h->cfg.path = 0;
   h->cfg.update_block = 256;
   h->cfg.deliver_warps = 4;
-  h->cfg.fused_block = 256;
-  h->cfg.fused_items_per_sm = 2;
+  h->cfg.fused_block = 128;
+  h->cfg.fused_items_per_sm = 8;
   h->cfg.window_steps = (int32_t)h->L.window;
   h->cfg.deliver_chunk = 384;
   h->cfg.update_groups = 2;
@@ -695,7 +695,8 @@ static int run_fused(snn_net *const *hs, const uint64_t *steps, int32_t n) {
     B.pinned_nets[i] = d;
   }
   const int sms = hs[0]->sm_count > 0 ? hs[0]->sm_count : 148;
-  const int blocks = (int)std::max<size_t>(1, std::min<size_t>(n_items, (size_t)sms * cfg.fused_items_per_sm));
+  const int per_sm = std::min(cfg.fused_items_per_sm, fused_blocks_per_sm(block));
+  const int blocks = (int)std::max<size_t>(1, std::min<size_t>(n_items, (size_t)sms * per_sm));
   if (!B.exec || B.exec_window != window || B.exec_items != (uint32_t)n_items || B.exec_block != block ||
       B.exec_blocks != blocks || B.exec_chunk != chunk) {
     if (B.exec) { cudaGraphExecDestroy(B.exec); B.exec = nullptr; }
@@ -934,7 +935,7 @@ extern "C" int snn_set_launch(snn_handle h, const snn_launch *cfg) {
   if (c.deliver_warps < 1 || c.deliver_warps > 8) return fail(SNN_ERR_ARG, "deliver_warps must be in 1..8");
   if (c.fused_block < 128 || c.fused_block > 512 || c.fused_block % 32)
     return fail(SNN_ERR_ARG, "fused_block must be a multiple of 32 in 128..512");
-  if (c.fused_items_per_sm < 1 || c.fused_items_per_sm > 8) return fail(SNN_ERR_ARG, "fused_items_per_sm in 1..8");
+  if (c.fused_items_per_sm < 1 || c.fused_items_per_sm > 32) return fail(SNN_ERR_ARG, "fused_items_per_sm in 1..32");
   if (c.window_steps < 1 || c.window_steps > 4096) return fail(SNN_ERR_ARG, "window_steps in 1..4096");
   if (c.deliver_chunk < 8 || c.deliver_chunk % 8 || (uint32_t)c.deliver_chunk > max_chunk_records())
     return fail(SNN_ERR_ARG, "deliver_chunk must be a multiple of 8 in 8..1152");
@@ -995,9 +996,9 @@ extern "C" int snn_autotune(snn_handle h, uint32_t trial_steps) {
           c.deliver_chunk = ch;
           cands.push_back(c);
         }
-  for (int fb : {128, 256, 512})
-    for (int ips : {1, 2, 4})
-      for (int ch : {576, 288, 144}) {
+  for (int fb : {128, 256})
+    for (int ips : {4, 8, 16})
+      for (int ch : {256, 128}) {
         snn_launch c = orig;
         c.path = 1;
         c.fused_block = fb;

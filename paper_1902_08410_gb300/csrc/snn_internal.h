@@ -107,6 +107,7 @@ cudaError_t launch_deliver(const NetDev &nd, uint32_t k, uint32_t chunk, int war
 cudaError_t launch_fused(const FusedTable &tab, uint32_t k, int block, int blocks, cudaStream_t s);
 uint32_t max_chunk_records();        // largest chunk of the two-kernel delivery
 uint32_t max_fused_chunk_records();  // largest chunk of the fused step
+int fused_blocks_per_sm(int block);   // resident fused blocks per SM
 int device_sm_count();
 
 }  // namespace snn

@@ -101,6 +101,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
 
 constexpr uint32_t kDefaultWaitLimit = 1u << 22;
 
+// Programmatic dependent launch: wait for the previous kernel in the stream
+// (no-op when launched without the attribute), then let the next one launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // Fire-and-forget global reductions (no value returned, no scoreboard wait).
 // ---------------------------------------------------------------------------
@@ -422,7 +427,7 @@ __device__ bool deliver_items(const NetDev &nd, WarpStage &ws, uint32_t chunk, u
 }
 
 constexpr uint32_t kStageCap = 1152;   // records per staging buffer of k_deliver (f32: 9216 B)
-constexpr uint32_t kFusedCap = 576;    // records per staging buffer of k_fused
+constexpr uint32_t kFusedCap = 256;    // records per staging buffer of k_fused
 
 uint32_t max_chunk_records() { return kStageCap; }
 uint32_t max_fused_chunk_records() { return kFusedCap; }
@@ -658,11 +663,15 @@ __global__ void __launch_bounds__(256) k_deliver(const __grid_constant__ NetDev 
 // Kernel: fused step over a table of networks.  A block takes work items
 // (network, 4*blockDim neurons): update, recording and a block-local spike
 // list, then its warps deliver those spikes.  Update reads ring slot t and
-// delivery writes slots t+1..t+D-1, so blocks need no grid-wide barrier.
+// delivery writes slots t+1..t+D-1, so blocks need no grid-wide barrier; many
+// small blocks per SM let one block's update overlap another's delivery.
+// Launched with programmatic dependent launch: the prologue (barrier set-up,
+// descriptor copy, window read) runs while the previous step drains.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(512) k_fused(const __grid_constant__ FusedTable tab, uint32_t k) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ NetDev nd;
+  __shared__ NetWin s_win;
   __shared__ uint64_t s_bars[32];
   __shared__ uint32_t s_count;
   __shared__ uint32_t s_net;
@@ -673,6 +682,7 @@ __global__ void __launch_bounds__(512) k_fused(const __grid_constant__ FusedTabl
   WarpStage ws;
   init_stage(ws, stage_base + (size_t)warp * 2u * kFusedCap * 8u, s_bars + 2 * warp, kFusedCap);
   if (threadIdx.x == 0) s_net = 0xFFFFFFFFu;
+  bool waited = false;
   for (uint32_t it = blockIdx.x; it < tab.n_items; it += gridDim.x) {
     const FusedItem item = tab.items[it];
     __syncthreads();   // the previous item is done with shared memory
@@ -680,26 +690,35 @@ __global__ void __launch_bounds__(512) k_fused(const __grid_constant__ FusedTabl
       const uint32_t *src = reinterpret_cast<const uint32_t *>(tab.nets + item.net);
       uint32_t *dst = reinterpret_cast<uint32_t *>(&nd);
       for (uint32_t i = threadIdx.x; i < sizeof(NetDev) / 4; i += blockDim.x) dst[i] = src[i];
+      if (threadIdx.x == 0) s_win = *reinterpret_cast<const NetWin *>(tab.nets[item.net].win);
     }
     if (threadIdx.x == 0) s_count = 0u;
     __syncthreads();
     if (threadIdx.x == 0) s_net = item.net;
-    const NetWin w = *nd.win;
-    const uint32_t t = w.t0 + k;
-    if (t >= w.t_end) continue;
+    const uint32_t t = s_win.t0 + k;
+    if (t >= s_win.t_end) continue;
+    if (!waited) {     // everything below reads what the previous step wrote
+      pdl_wait();
+      pdl_trigger();
+      waited = true;
+    }
     const uint32_t n0 = item.n_begin + threadIdx.x * 4u;
     const uint32_t warp_first = item.n_begin + warp * 128u;
     if (warp_first < nd.N_pad) {
       uint32_t n_ext[1] = {0};
       const uint32_t mask[1] = {update4(nd, n0, t, n_ext[0])};
       const uint32_t a1[1] = {n0};
-      record_warp<1>(nd, mask, a1, n_ext, t, k, w.bin0, s_ids, &s_count);
+      record_warp<1>(nd, mask, a1, n_ext, t, k, s_win.bin0, s_ids, &s_count);
     }
     __syncthreads();
     const uint32_t cnt = s_count;
     if (cnt == 0) continue;
     const uint32_t nch = (nd.M_pad + tab.chunk - 1u) / tab.chunk;
     deliver_items(nd, ws, tab.chunk, warp, nw, cnt * nch, t % nd.D, [&](uint32_t s) { return s_ids[s]; });
+  }
+  if (!waited) {
+    pdl_wait();
+    pdl_trigger();
   }
 }
 
@@ -767,8 +786,24 @@ cudaError_t launch_deliver(const NetDev &nd, uint32_t k, uint32_t chunk, int war
 cudaError_t launch_fused(const FusedTable &tab, uint32_t k, int block, int blocks, cudaStream_t s) {
   if (block < 128 || block > 512 || (block % 32)) return cudaErrorInvalidValue;
   if (tab.chunk < 8 || tab.chunk > kFusedCap || (tab.chunk % 8)) return cudaErrorInvalidValue;
-  k_fused<<<blocks, block, fused_smem_bytes(block), s>>>(tab, k);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = fused_smem_bytes(block);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_fused, tab, k);
+}
+
+int fused_blocks_per_sm(int block) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused, block, fused_smem_bytes(block)) != cudaSuccess)
+    return 1;
+  return n > 0 ? n : 1;
 }
 
 }  // namespace snn
