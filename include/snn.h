@@ -183,6 +183,32 @@ int snn_autotune(snn_handle h, uint32_t trial_steps);
  * snn_run; the call exists to measure kernels without a profiler. */
 int snn_time_kernels(snn_handle h, uint32_t steps, double *ms_out);
 
+/* Build the synapse rows of a network (the same construction and the same
+ * bytes as snn_build_network) into device memory the caller owns, with no
+ * device allocation by the library.  The paper has no counterpart of this
+ * call; it exists for callers that cannot let a library call cudaMalloc (a
+ * program whose device memory is all handed out by its own pool allocator, a
+ * real-time loop that cannot take cudaMalloc's latency and synchronisation,
+ * a process that has reserved nearly all device memory).
+ *   rows_out:   device pointer, 16-byte aligned, receives N rows of
+ *               row_bytes = 4 * M_pad + (4 or 2) * M_pad bytes (M_pad = M rounded
+ *               up to 8): M_pad record keys (delay << 24 | target), then M_pad
+ *               weights (f32 mV, or i16 in 2^-10 mV for SNN_REC_I16), records in
+ *               delay order, padding records zero.  NULL queries the size.
+ *   rows_bytes: in: bytes available at rows_out; out: bytes required.
+ *   cuda_stream: stream the copies and the kernel are ordered on; the call
+ *               returns once they are enqueued.
+ * Scratch (module thresholds, Gaussian table) lives in one static device array
+ * of about 4.2 MB that every GPU loading the library holds until exit, so the
+ * grid may have at most 1024 modules (SNN_ERR_LIMIT beyond).  The first call
+ * on a device looks up that array's address; make it before any stream
+ * capture.  All calls share the array: calls whose work overlaps on the GPU
+ * race and must be ordered by the caller (for example on one stream).
+ * Errors: SNN_ERR_ARG, SNN_ERR_LIMIT, SNN_ERR_BUFFER (rows_bytes too small),
+ * SNN_ERR_CUDA. */
+int snn_build_rows_static(const snn_params *p, uint64_t seed, void *rows_out, size_t *rows_bytes,
+                          void *cuda_stream);
+
 /* Release the network and its device memory. */
 void snn_free(snn_handle h);
 

@@ -22,7 +22,7 @@ INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "--expt-relaxed-constexpr",
               "-Xcompiler", "-fPIC,-ffp-contract=off,-O2,-fno-fast-math", f"-I{INCLUDE}"]
-SOURCES = ["snn_kernels.cu", "snn_host.cpp"]
+SOURCES = ["snn_kernels.cu", "snn_host.cpp", "snn_noalloc.cu"]
 HEADERS = ["snn_internal.h"]
 
 
@@ -105,7 +105,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 EXPORTS = ["snn_set_allocator", "snn_footprint", "snn_build_network", "snn_run", "snn_run_batch",
            "snn_read_spikes", "snn_rates", "snn_read_state", "snn_read_row", "snn_get_stats",
            "snn_get_launch", "snn_set_launch", "snn_autotune", "snn_free", "snn_last_error",
-           "snn_debug_set_wait_limit", "snn_time_kernels"]
+           "snn_debug_set_wait_limit", "snn_time_kernels", "snn_build_rows_static"]
 
 _lib = None
 
@@ -140,6 +140,7 @@ def load(build_if_needed: bool = True):
         "snn_last_error": ([], ctypes.c_char_p),
         "snn_debug_set_wait_limit": ([vp, u32], ctypes.c_int),
         "snn_time_kernels": ([vp, u32, P(ctypes.c_double)], ctypes.c_int),
+        "snn_build_rows_static": ([P(SnnParams), u64, vp, P(sz), vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)

@@ -27,7 +27,9 @@ using namespace snn;
 // ---------------------------------------------------------------------------
 static thread_local std::string g_last_error;
 
-static int fail(int code, const std::string &msg) {
+int snn_fail(int code, const std::string &msg);
+static int fail(int code, const std::string &msg) { return snn_fail(code, msg); }
+int snn_fail(int code, const std::string &msg) {
   g_last_error = msg;
   return code;
 }
@@ -104,7 +106,7 @@ static int dev_alloc(DevBuf &b, size_t bytes) {
 // ---------------------------------------------------------------------------
 // host tables (FP64, rounded once)
 // ---------------------------------------------------------------------------
-namespace {
+namespace snn {
 
 double std_normal_cdf(double x) { return 0.5 * std::erfc(-x / std::sqrt(2.0)); }
 
@@ -208,7 +210,22 @@ void module_thresholds(const snn_params &p, std::vector<uint32_t> &out) {
   }
 }
 
-}  // namespace
+void gaussian_table(std::vector<float> &ztab) {
+  ztab.resize(kZTab);
+  for (int i = 0; i < kZTab; ++i) ztab[i] = (float)inverse_normal_cdf(((double)i + 0.5) / (double)kZTab);
+}
+
+void build_inputs(const snn_params &p, BuildDev &bd) {
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      bd.J[a][b] = p.J[a][b];
+      bd.sig[a][b] = p.dJ_frac * std::fabs(p.J[a][b]);
+    }
+  bd.n_delay = (uint32_t)p.n_delay;
+  bd.p_local_mode = p.p_local >= 0.0f ? 1 : 0;
+}
+
+}  // namespace snn
 
 // ---------------------------------------------------------------------------
 // network object
@@ -226,7 +243,9 @@ struct Layout {
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-static int validate(const snn_params &p) {
+int snn_validate_params(const snn_params &p);
+static int validate(const snn_params &p) { return snn_validate_params(p); }
+int snn_validate_params(const snn_params &p) {
   if (p.gx < 1 || p.gy < 1) return fail(SNN_ERR_ARG, "grid must be at least 1x1");
   if (!(p.lambda > 0.0f) || !std::isfinite(p.lambda)) return fail(SNN_ERR_ARG, "lambda must be > 0");
   if (!std::isfinite(p.p_local) || p.p_local > 1.0f) return fail(SNN_ERR_ARG, "p_local must be <= 1");
@@ -440,8 +459,8 @@ extern "C" int snn_build_network(const snn_params *p, uint64_t seed, void *cuda_
   uint8_t *base = static_cast<uint8_t *>(h->arena.p);
 
   // tables for construction and the external drive
-  std::vector<float> ztab(kZTab);
-  for (int i = 0; i < kZTab; ++i) ztab[i] = (float)inverse_normal_cdf(((double)i + 0.5) / (double)kZTab);
+  std::vector<float> ztab;
+  gaussian_table(ztab);
   std::vector<int32_t> amp((size_t)kNPop * kZTab);
   for (int q = 0; q < 3; ++q) {
     const float sig = p->dJ_ext_frac * std::fabs(p->J_ext[q]);
@@ -454,13 +473,7 @@ extern "C" int snn_build_network(const snn_params *p, uint64_t seed, void *cuda_
   std::vector<uint32_t> cdf;
   module_thresholds(*p, cdf);
   BuildDev bd{};
-  for (int a = 0; a < 3; ++a)
-    for (int b = 0; b < 3; ++b) {
-      bd.J[a][b] = p->J[a][b];
-      bd.sig[a][b] = p->dJ_frac * std::fabs(p->J[a][b]);
-    }
-  bd.n_delay = (uint32_t)p->n_delay;
-  bd.p_local_mode = p->p_local >= 0.0f ? 1 : 0;
+  build_inputs(*p, bd);
   DevBuf tmp;
   const size_t cdf_bytes = std::max<size_t>(cdf.size() * 4, 16);
   rc = dev_alloc(tmp, align_up(cdf_bytes, 256) + kZTab * 4);

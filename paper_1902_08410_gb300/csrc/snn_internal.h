@@ -111,3 +111,15 @@ int fused_blocks_per_sm(int block);   // resident fused blocks per SM
 int device_sm_count();
 
 }  // namespace snn
+
+// ---- host helpers shared by the host translation units (snn_host.cpp) ----
+#include <string>
+#include <vector>
+struct snn_params;
+namespace snn {
+void module_thresholds(const snn_params &p, std::vector<uint32_t> &out);   // Eq. 1 thresholds [G][G-1]
+void gaussian_table(std::vector<float> &ztab);                             // Phi^-1((i + 0.5) / 4096)
+void build_inputs(const snn_params &p, BuildDev &bd);                      // efficacy means and spreads
+}  // namespace snn
+int snn_validate_params(const snn_params &p);   // SNN_OK or an error code (message set)
+int snn_fail(int code, const std::string &msg);  // set the thread's last error, return code
