@@ -55,6 +55,15 @@ def parse_args():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mode", choices=["grid", "batch", "serve"], default="grid",
+                    help="grid: 24x24 SWA+AW (default); batch: 256-network SWA->AW sweep; serve: request stream")
+    ap.add_argument("--batch-nets", type=int, default=256)
+    ap.add_argument("--batch-steps", type=int, default=20_000)
+    ap.add_argument("--plain-steps", type=int, default=2_000)
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--rate", type=float, default=0.0, help="requests/s; 0 = 0.8 x measured capacity")
+    ap.add_argument("--duration-scale", type=float, default=1.0)
+    ap.add_argument("--chunk-steps", type=int, default=1000)
     return ap.parse_args()
 
 
@@ -379,8 +388,131 @@ def run_gb300(args, dist: Dist):
         n.close()
 
 
+# ---------------------------------------------------------------------------
+# batched sweep: one fused kernel per step over all networks vs one network per launch
+# ---------------------------------------------------------------------------
+def run_batch_mode(args, dist: Dist):
+    import numpy as np
+    import torch
+    torch.cuda.set_device(dist.local_rank)
+    import paper_1902_08410_gb300 as snn
+    snn.build()
+    specs = W.batched_sweep(n_nets=args.batch_nets, steps=args.batch_steps)
+    t0 = time.perf_counter()
+    nets = [snn.Network(sp["params"], sp["seed"] + 7919 * dist.rank) for sp in specs]
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    for n in nets:
+        n.launch = {"path": 1}
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(gpu_selector(dist.local_rank))
+    sampler.start()
+    e0.record(stream)
+    snn.run_batch(nets, [args.batch_steps] * len(nets))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    t_batch = e0.elapsed_time(e1) / 1e3
+    ev_batch = sum(n.stats()["spikes"] for n in nets) * EQUIV_PER_SPIKE
+    neurons = sum(n.N for n in nets)
+    # one network per launch (two kernels per step, each network alone), fresh copies
+    ev_plain, t_plain, same = 0, 0.0, 0
+    for sp, bn in zip(specs, nets):
+        n = snn.Network(sp["params"], sp["seed"] + 7919 * dist.rank)
+        n.launch = {"path": 0}
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        n.run(args.plain_steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_plain += a.elapsed_time(b) / 1e3
+        ev_plain += n.stats()["spikes"] * EQUIV_PER_SPIKE
+        ps, pi = n.spikes()
+        bs, bi = bn.spikes(0, args.plain_steps)
+        same += int(np.array_equal(ps, bs) and np.array_equal(pi, bi))
+        n.close()
+    t_b = dist.reduce(t_batch, "max")
+    line = {
+        "metric": METRIC, "mode": "batch", "value": dist.reduce(float(ev_batch), "sum") / t_b, "unit": UNIT,
+        "n_gpus": dist.world, "higher_is_better": True, "data": "synthetic", "dtype": "f32+i32",
+        "config": {"workload": f"{len(nets)} networks, sides U{{2..8}}, g_c on a 16-point SWA->AW grid, "
+                               f"nu_ext U[2, 8] Hz, i16 records, {args.batch_steps} steps each",
+                   "neurons": neurons, "recurrent_synapses": sum(n.N * n.M for n in nets)},
+        "batched": {"events_per_s": ev_batch / t_batch, "seconds": t_batch, "steps": args.batch_steps,
+                    "us_per_step": 1e6 * t_batch / args.batch_steps},
+        "one_network_per_launch": {"events_per_s": ev_plain / t_plain, "seconds": t_plain,
+                                   "steps": args.plain_steps},
+        "speedup": (ev_batch / t_batch) / (ev_plain / t_plain),
+        "identical_rasters": f"{same}/{len(nets)} networks (first {args.plain_steps} steps)",
+        "build_seconds": build_s, "clocks": clocks,
+    }
+    for n in nets:
+        n.close()
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# serving: Poisson-arrival stream of requests, continuous batching
+# ---------------------------------------------------------------------------
+def run_serve_mode(args, dist: Dist):
+    import numpy as np
+    import torch
+    torch.cuda.set_device(dist.local_rank)
+    import paper_1902_08410_gb300 as snn
+    from paper_1902_08410_gb300.serve import Server
+    snn.build()
+    free, total = torch.cuda.mem_get_info()
+    budget = int(free * 0.8)
+    reqs = W.serving_requests(n_req=args.requests, rate_hz=1.0)
+    for r in reqs:
+        r["steps"] = max(1, int(round(r["steps"] * args.duration_scale)))
+    rate = args.rate
+    if rate <= 0:
+        # capacity: neuron-steps per second of the batched path on the first requests
+        sample = reqs[:min(64, len(reqs))]
+        nets = [snn.Network(r["params"], r["seed"]) for r in sample]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        snn.run_batch(nets, [1000] * len(nets))
+        torch.cuda.synchronize()
+        rate_ns = sum(n.N for n in nets) * 1000 / (time.perf_counter() - t0)
+        for n in nets:
+            n.close()
+        work = np.mean([W.n_neurons(r["params"]) * r["steps"] for r in reqs])
+        rate = 0.8 * rate_ns / work
+    # arrivals: unit-rate stream rescaled to the chosen rate
+    srv = Server(memory_budget=budget, chunk_steps=args.chunk_steps, realtime=True)
+    for r in reqs:
+        srv.submit(r["params"], r["seed"], r["steps"], arrival_s=r["arrival_s"] / rate)
+    out = srv.run()
+    lat = np.array([x.latency_s for x in out["results"]])
+    line = {
+        "metric": "serving latency and aggregate synaptic events/s", "mode": "serve",
+        "p50_latency_s": out["p50_latency_s"], "p99_latency_s": out["p99_latency_s"],
+        "mean_latency_s": float(lat.mean()), "events_per_s": out["events_per_s"], "unit": UNIT,
+        "requests": len(reqs), "rate_per_s": rate, "wall_s": out["wall_s"], "chunks": out["chunks"],
+        "config": {"workload": f"{len(reqs)} requests, sides round(2^U(1,4)), durations U[0.5, 10] s x "
+                               f"{args.duration_scale}, SWA/AW 50/50, i16 records, Poisson arrivals",
+                   "memory_budget_bytes": budget, "chunk_steps": args.chunk_steps},
+        "data": "synthetic", "n_gpus": dist.world,
+    }
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.mode in ("batch", "serve"):
+        dist = Dist("nccl")
+        try:
+            (run_batch_mode if args.mode == "batch" else run_serve_mode)(args, dist)
+        finally:
+            dist.close()
+        return
     if args.impl == "reference":
         dist = Dist("gloo")
         try:

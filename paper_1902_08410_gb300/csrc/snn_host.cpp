@@ -284,7 +284,7 @@ static Layout make_layout(const snn_params &p) {
   // A neuron fires at most once per narp_min + 1 steps, so a window of W steps
   // holds at most N * ceil(W / (narp_min + 1)) raster entries: size the window
   // so that this bound fits the entry budget, and the raster can never overflow.
-  const size_t budget = 192ull << 20;
+  const size_t budget = std::min<size_t>(192ull << 20, std::max<size_t>(8ull << 20, (size_t)L.N * 256u));
   const size_t per_step = (size_t)L.N * 8u / (size_t)(narp_min + 1) + 8u;
   L.window = (uint32_t)std::max<size_t>(16, std::min<size_t>(1024, budget / per_step));
   L.rec_cap = (uint32_t)std::min<uint64_t>(0xFFFFFFF0ull,
@@ -545,15 +545,25 @@ static int capture_window(snn_net *h, uint32_t window) {
   return SNN_OK;
 }
 
-// Copy a finished window's records to host memory and reset them on the device.
-static int drain_window(snn_net *h, uint64_t t0, cudaStream_t s) {
+// Draining a finished window's records happens in three phases so that a
+// batch of networks needs two host synchronisations per window in total:
+// (1) copy the recording block (header, external-event slots, rates) to
+// pinned memory; (2) after a sync, check the status and copy the raster
+// entries; (3) after a sync, append them and reset the device block.
+static int drain_copy_block(snn_net *h, cudaStream_t s) {
   const Layout &L = h->L;
   uint8_t *base = static_cast<uint8_t *>(h->arena.p);
   const size_t rec_bytes = L.off_entries - L.off_rec;
   CU_TRY(cudaMemcpyAsync(h->pinned_rec, base + L.off_rec, rec_bytes, cudaMemcpyDeviceToHost, s));
-  CU_TRY(cudaStreamSynchronize(s));
   h->d2h += rec_bytes;
+  return SNN_OK;
+}
+
+static int drain_copy_entries(snn_net *h, cudaStream_t s, uint32_t *n_out) {
+  const Layout &L = h->L;
+  uint8_t *base = static_cast<uint8_t *>(h->arena.p);
   const RecHeader *rh = reinterpret_cast<const RecHeader *>(h->pinned_rec);
+  *n_out = 0;
   if (rh->status & kStatusTimeout) {
     h->broken = true;
     return fail(SNN_ERR_TIMEOUT, "a bounded wait on an asynchronous copy gave up; the network is invalid");
@@ -563,9 +573,6 @@ static int drain_window(snn_net *h, uint64_t t0, cudaStream_t s) {
     return fail(SNN_ERR_LIMIT, "spike record window overflowed");
   }
   const uint32_t n_rec = std::min(rh->cursor, L.rec_cap);
-  h->spikes += n_rec;
-  const unsigned long long *ext = reinterpret_cast<const unsigned long long *>(h->pinned_rec + (L.off_ext - L.off_rec));
-  for (uint32_t i = 0; i < L.n_ext_slots; ++i) h->ext_events += ext[i];
   if (n_rec) {
     if (h->pinned_entries_cap < n_rec) {
       if (h->pinned_entries) cudaFreeHost(h->pinned_entries);
@@ -576,8 +583,19 @@ static int drain_window(snn_net *h, uint64_t t0, cudaStream_t s) {
       h->pinned_entries_cap = cap;
     }
     CU_TRY(cudaMemcpyAsync(h->pinned_entries, base + L.off_entries, (size_t)n_rec * 8, cudaMemcpyDeviceToHost, s));
-    CU_TRY(cudaStreamSynchronize(s));
     h->d2h += (uint64_t)n_rec * 8;
+  }
+  *n_out = n_rec;
+  return SNN_OK;
+}
+
+static int drain_absorb(snn_net *h, uint64_t t0, uint32_t n_rec, cudaStream_t s) {
+  const Layout &L = h->L;
+  uint8_t *base = static_cast<uint8_t *>(h->arena.p);
+  h->spikes += n_rec;
+  const unsigned long long *ext = reinterpret_cast<const unsigned long long *>(h->pinned_rec + (L.off_ext - L.off_rec));
+  for (uint32_t i = 0; i < L.n_ext_slots; ++i) h->ext_events += ext[i];
+  if (n_rec) {
     const size_t old = h->raster.size();
     h->raster.resize(old + n_rec);
     for (uint32_t i = 0; i < n_rec; ++i) {
@@ -593,7 +611,46 @@ static int drain_window(snn_net *h, uint64_t t0, cudaStream_t s) {
   const size_t need = (size_t)(bin0 + L.rates_bins) * per_bin;
   if (h->rates.size() < need) h->rates.resize(need, 0u);
   for (size_t i = 0; i < (size_t)L.rates_bins * per_bin; ++i) h->rates[bin0 * per_bin + i] += rw[i];
-  CU_TRY(cudaMemsetAsync(base + L.off_rec, 0, rec_bytes, s));
+  CU_TRY(cudaMemsetAsync(base + L.off_rec, 0, L.off_entries - L.off_rec, s));
+  return SNN_OK;
+}
+
+// Copy a finished window's records of one network to host memory and reset them.
+static int drain_window(snn_net *h, uint64_t t0, cudaStream_t s) {
+  int rc = drain_copy_block(h, s);
+  if (rc) return rc;
+  CU_TRY(cudaStreamSynchronize(s));
+  uint32_t n_rec = 0;
+  rc = drain_copy_entries(h, s, &n_rec);
+  if (rc) return rc;
+  if (n_rec) CU_TRY(cudaStreamSynchronize(s));
+  return drain_absorb(h, t0, n_rec, s);
+}
+
+// The same for every network of a batch, with two synchronisations in total.
+static int drain_batch(snn_net *const *hs, const uint64_t *t0s, const uint64_t *adv, int32_t n, cudaStream_t s) {
+  for (int i = 0; i < n; ++i)
+    if (adv[i]) {
+      int rc = drain_copy_block(hs[i], s);
+      if (rc) return rc;
+    }
+  CU_TRY(cudaStreamSynchronize(s));
+  std::vector<uint32_t> n_rec(n, 0);
+  bool any = false;
+  int first_err = SNN_OK;
+  for (int i = 0; i < n; ++i)
+    if (adv[i]) {
+      int rc = drain_copy_entries(hs[i], s, &n_rec[i]);
+      if (rc && first_err == SNN_OK) first_err = rc;
+      any |= n_rec[i] != 0;
+    }
+  if (any) CU_TRY(cudaStreamSynchronize(s));
+  if (first_err) return first_err;
+  for (int i = 0; i < n; ++i)
+    if (adv[i]) {
+      int rc = drain_absorb(hs[i], t0s[i], n_rec[i], s);
+      if (rc) return rc;
+    }
   return SNN_OK;
 }
 
@@ -629,6 +686,7 @@ struct BatchCtx {
   DevBuf nets;                 // NetDev[cap]
   DevBuf wins;                 // NetWin[cap]
   DevBuf items;                // FusedItem[item_cap]
+  DevBuf n_items_dev;          // u32 item count read by the kernel
   size_t cap = 0, item_cap = 0;
   NetDev *pinned_nets = nullptr;
   NetWin *pinned_wins = nullptr;
@@ -636,6 +694,7 @@ struct BatchCtx {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t exec = nullptr;
   uint32_t exec_window = 0, exec_items = 0, exec_chunk = 0;
+  uint32_t pinned_count = 0;   // staging of the item count (copied before the replays)
   int exec_block = 0, exec_blocks = 0;
   ~BatchCtx() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -646,6 +705,7 @@ struct BatchCtx {
     nets.release();
     wins.release();
     items.release();
+    n_items_dev.release();
   }
 };
 static thread_local std::unique_ptr<BatchCtx> g_batch;
@@ -693,6 +753,10 @@ static int run_fused(snn_net *const *hs, const uint64_t *steps, int32_t n) {
     if (B.exec) { cudaGraphExecDestroy(B.exec); B.exec = nullptr; }
   }
   if (!B.cap_stream) CU_TRY(cudaStreamCreateWithFlags(&B.cap_stream, cudaStreamNonBlocking));
+  if (!B.n_items_dev.p) {
+    int rc = dev_alloc(B.n_items_dev, 256);
+    if (rc) return rc;
+  }
   cudaStream_t s = hs[0]->stream;
   // all networks of the batch are ordered on the first network's stream
   for (int i = 0; i < n; ++i)
@@ -709,12 +773,12 @@ static int run_fused(snn_net *const *hs, const uint64_t *steps, int32_t n) {
   }
   const int sms = hs[0]->sm_count > 0 ? hs[0]->sm_count : 148;
   const int per_sm = std::min(cfg.fused_items_per_sm, fused_blocks_per_sm(block));
-  const int blocks = (int)std::max<size_t>(1, std::min<size_t>(n_items, (size_t)sms * per_sm));
-  if (!B.exec || B.exec_window != window || B.exec_items != (uint32_t)n_items || B.exec_block != block ||
-      B.exec_blocks != blocks || B.exec_chunk != chunk) {
+  const int blocks = sms * per_sm;   // fixed grid: the same graph serves any set of networks
+  if (!B.exec || B.exec_window != window || B.exec_block != block || B.exec_blocks != blocks ||
+      B.exec_chunk != chunk) {
     if (B.exec) { cudaGraphExecDestroy(B.exec); B.exec = nullptr; }
     FusedTable tab{static_cast<const NetDev *>(B.nets.p), static_cast<const FusedItem *>(B.items.p),
-                   (uint32_t)n_items, chunk};
+                   static_cast<const uint32_t *>(B.n_items_dev.p), chunk};
     CU_TRY(cudaStreamBeginCapture(B.cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t err = cudaSuccess;
     for (uint32_t k = 0; k < window && err == cudaSuccess; ++k) err = launch_fused(tab, k, block, blocks, B.cap_stream);
@@ -735,6 +799,8 @@ static int run_fused(snn_net *const *hs, const uint64_t *steps, int32_t n) {
     B.exec_chunk = chunk;
   }
   CU_TRY(cudaMemcpyAsync(B.items.p, B.pinned_items, n_items * sizeof(FusedItem), cudaMemcpyHostToDevice, s));
+  B.pinned_count = (uint32_t)n_items;
+  CU_TRY(cudaMemcpyAsync(B.n_items_dev.p, &B.pinned_count, 4, cudaMemcpyHostToDevice, s));
   CU_TRY(cudaMemcpyAsync(B.nets.p, B.pinned_nets, (size_t)n * sizeof(NetDev), cudaMemcpyHostToDevice, s));
   std::vector<uint64_t> left(steps, steps + n);
   while (true) {
@@ -754,14 +820,16 @@ static int run_fused(snn_net *const *hs, const uint64_t *steps, int32_t n) {
     CU_TRY(cudaGraphLaunch(B.exec, s));
     hs[0]->launches += window;   // one fused kernel per step for the whole batch
     for (int i = 0; i < n; ++i) hs[i]->h2d += sizeof(NetWin) + sizeof(NetDev);
+    std::vector<uint64_t> t0s(n), adv(n);
     for (int i = 0; i < n; ++i) {
-      snn_net *h = hs[i];
-      const uint64_t adv = std::min<uint64_t>(window, left[i]);
-      if (adv == 0) continue;
-      int rc = drain_window(h, h->t, s);
-      if (rc) return rc;
-      h->t += adv;
-      left[i] -= adv;
+      t0s[i] = hs[i]->t;
+      adv[i] = std::min<uint64_t>(window, left[i]);
+    }
+    int rc = drain_batch(hs, t0s.data(), adv.data(), n, s);
+    if (rc) return rc;
+    for (int i = 0; i < n; ++i) {
+      hs[i]->t += adv[i];
+      left[i] -= adv[i];
     }
   }
   return SNN_OK;

@@ -94,8 +94,8 @@ struct FusedItem {
 struct FusedTable {
   const NetDev *nets;
   const FusedItem *items;
-  uint32_t n_items;
-  uint32_t chunk;       // records per delivery chunk
+  const uint32_t *n_items;  // item count in device memory (the graph outlives any one batch)
+  uint32_t chunk;           // records per delivery chunk
 };
 
 // ---- launchers (snn_kernels.cu) -------------------------------------------

@@ -683,7 +683,8 @@ __global__ void __launch_bounds__(512) k_fused(const __grid_constant__ FusedTabl
   init_stage(ws, stage_base + (size_t)warp * 2u * kFusedCap * 8u, s_bars + 2 * warp, kFusedCap);
   if (threadIdx.x == 0) s_net = 0xFFFFFFFFu;
   bool waited = false;
-  for (uint32_t it = blockIdx.x; it < tab.n_items; it += gridDim.x) {
+  const uint32_t n_items = *tab.n_items;
+  for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
     const FusedItem item = tab.items[it];
     __syncthreads();   // the previous item is done with shared memory
     if (s_net != item.net) {
