@@ -55,8 +55,11 @@ def parse_args():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mode", choices=["grid", "batch", "serve"], default="grid",
-                    help="grid: 24x24 SWA+AW (default); batch: 256-network SWA->AW sweep; serve: request stream")
+    ap.add_argument("--mode", choices=["grid", "batch", "serve", "grid64"], default="grid",
+                    help="grid: 24x24 SWA+AW (default); batch: 256-network SWA->AW sweep; serve: request "
+                         "stream; grid64: 64x64 lambda sweep with f32 vs i16 records")
+    ap.add_argument("--grid64-steps", type=int, default=50_000)
+    ap.add_argument("--grid64-lambdas", type=str, default="0.4,1.0,2.0")
     ap.add_argument("--batch-nets", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=20_000)
     ap.add_argument("--plain-steps", type=int, default=2_000)
@@ -504,12 +507,84 @@ def run_serve_mode(args, dist: Dist):
         print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# 64x64 grid: lambda sweep, SWA and AW, f32 vs packed i16 records
+# ---------------------------------------------------------------------------
+def _swa_frequency(rates, bin_s):
+    """Dominant frequency (Hz) of the whole-network rate in 0.2..10 Hz (Welch PSD, Sec. 2.3)."""
+    import numpy as np
+    from scipy.signal import welch
+    x = rates.sum(axis=(1, 2)).astype(np.float64)
+    x = x[len(x) // 10:]                      # drop the initial transient
+    x = x - x.mean()
+    f, pxx = welch(x, fs=1.0 / bin_s, nperseg=min(len(x), 512))
+    band = (f >= 0.2) & (f <= 10.0)
+    return float(f[band][np.argmax(pxx[band])]) if band.any() else None
+
+
+def run_grid64_mode(args, dist: Dist):
+    import numpy as np
+    import torch
+    torch.cuda.set_device(dist.local_rank)
+    import paper_1902_08410_gb300 as snn
+    snn.build()
+    runs = []
+    for lam in [float(x) for x in args.grid64_lambdas.split(",")]:
+        for reg in ("SWA", "AW"):
+            per_fmt = {}
+            for fmt in (W.REC_F32, W.REC_I16):
+                wl = W.grid_64x64(reg, lam, fmt)
+                t0 = time.perf_counter()
+                net = snn.Network(wl["params"], wl["seed"])
+                torch.cuda.synchronize()
+                build_s = time.perf_counter() - t0
+                net.run(2000)
+                cfg = net.autotune(100)
+                st0 = net.stats()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                net.run(args.grid64_steps)
+                e1.record()
+                torch.cuda.synchronize()
+                sec = e0.elapsed_time(e1) / 1e3
+                st1 = net.stats()
+                spikes = st1["spikes"] - st0["spikes"]
+                sim_s = args.grid64_steps * W.DT_MS * 1e-3
+                rates = net.rates()
+                pop = rates.sum(axis=(0, 1)).astype(np.float64)
+                dur = st1["t"] * W.DT_MS * 1e-3
+                pop_hz = (pop / (np.array(W.POP_SIZES) * net.G * dur)).tolist()
+                per_fmt[fmt] = {
+                    "format": "f32" if fmt == W.REC_F32 else "i16", "events_per_s": spikes * EQUIV_PER_SPIKE / sec,
+                    "sim_seconds_per_wall_second": sim_s / sec, "us_per_step": 1e6 * sec / args.grid64_steps,
+                    "rate_hz": spikes / (net.N * sim_s), "pop_rate_hz": pop_hz,
+                    "swa_frequency_hz": _swa_frequency(rates, W.BIN_STEPS * W.DT_MS * 1e-3),
+                    "bytes_per_recurrent_synapse": st1["device_bytes"] / st1["n_synapses"],
+                    "build_seconds": build_s, "launch": cfg,
+                }
+                net.close()
+            f, q = per_fmt[W.REC_F32], per_fmt[W.REC_I16]
+            runs.append({"lambda": lam, "regime": reg, "f32": f, "i16": q,
+                         "i16_vs_f32": {"rate_delta_rel": q["rate_hz"] / f["rate_hz"] - 1.0,
+                                        "swa_frequency_delta_hz": (None if f["swa_frequency_hz"] is None
+                                                                   or q["swa_frequency_hz"] is None
+                                                                   else q["swa_frequency_hz"] - f["swa_frequency_hz"]),
+                                        "speedup": q["events_per_s"] / f["events_per_s"]}})
+            if dist.rank == 0:
+                print(json.dumps(runs[-1]), flush=True)
+    if dist.rank == 0:
+        print(json.dumps({"metric": METRIC, "mode": "grid64", "unit": UNIT, "steps_per_run": args.grid64_steps,
+                          "runs": len(runs), "data": "synthetic",
+                          "config": {"workload": "64x64 grid, 5.12M neurons, 5.76G recurrent synapses"}}),
+              flush=True)
+
+
 def main():
     args = parse_args()
-    if args.mode in ("batch", "serve"):
+    if args.mode in ("batch", "serve", "grid64"):
         dist = Dist("nccl")
         try:
-            (run_batch_mode if args.mode == "batch" else run_serve_mode)(args, dist)
+            {"batch": run_batch_mode, "serve": run_serve_mode, "grid64": run_grid64_mode}[args.mode](args, dist)
         finally:
             dist.close()
         return

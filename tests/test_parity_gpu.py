@@ -229,3 +229,23 @@ def test_wait_limit_zero_reports_timeout(snn):
     g = snn.Network(p, 4)
     g.run(50)
     assert g.stats()["t"] == 50
+
+
+@pytest.mark.parametrize("fmt", [W.REC_F32, W.REC_I16])
+def test_run_64x64_first_steps(snn, oracle_mod, fmt):
+    """64x64 grid (5.12M neurons, 5.76G synapses) at full size: the first steps
+    (the oracle builds only the rows of neurons that fire) and sampled rows."""
+    p = W.base_params(64, 64, 1.0, "AW", record_format=fmt)
+    g = snn.Network(p, 1)
+    g.run(4)
+    o = _oracle(oracle_mod, p, 1, 4)
+    _assert_same_run(g, o, 4)
+    rng = np.random.default_rng(2)
+    for s in np.concatenate([[0, g.N - 1], rng.integers(0, g.N, 20)]):
+        gk, gw = g.row(int(s))
+        ok, ow = o.row(int(s))
+        assert np.array_equal(gk, ok), s
+        if fmt == W.REC_I16:
+            ow = np.clip(np.rint(ow * np.float32(1024.0)), -32768, 32767).astype(np.float32) / np.float32(1024.0)
+        assert np.array_equal(gw, ow), s
+    g.close()
