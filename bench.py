@@ -55,10 +55,20 @@ def parse_args():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mode", choices=["grid", "batch", "serve", "grid64"], default="grid",
+    ap.add_argument("--mode", choices=["grid", "batch", "serve", "grid64", "profile"], default="grid",
                     help="grid: 24x24 SWA+AW (default); batch: 256-network SWA->AW sweep; serve: request "
                          "stream; grid64: 64x64 lambda sweep with f32 vs i16 records")
     ap.add_argument("--grid64-steps", type=int, default=50_000)
+    # --mode profile: one network, fixed launch shape (the target of ncu captures)
+    ap.add_argument("--grid", type=int, default=24)
+    ap.add_argument("--regime", choices=["SWA", "AW"], default="AW")
+    ap.add_argument("--fmt", choices=["f32", "i16"], default="f32")
+    ap.add_argument("--path", type=int, choices=[0, 1], default=0)
+    ap.add_argument("--warm-steps", type=int, default=1024)
+    ap.add_argument("--run-steps", type=int, default=64)
+    ap.add_argument("--window", type=int, default=64)
+    ap.add_argument("--update-block", type=int, default=128)
+    ap.add_argument("--update-groups", type=int, default=1)
     ap.add_argument("--grid64-lambdas", type=str, default="0.4,1.0,2.0")
     ap.add_argument("--batch-nets", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=20_000)
@@ -579,12 +589,33 @@ def run_grid64_mode(args, dist: Dist):
               flush=True)
 
 
+def run_profile_mode(args, dist: Dist):
+    """One network, fixed launch shape: `warm-steps` steps, then `run-steps`
+    steps in windows of `window` steps (the kernels an ncu capture targets)."""
+    import torch
+    torch.cuda.set_device(dist.local_rank)
+    import paper_1902_08410_gb300 as snn
+    snn.build()
+    fmt = W.REC_F32 if args.fmt == "f32" else W.REC_I16
+    net = snn.Network(W.base_params(args.grid, args.grid, 1.0, args.regime, record_format=fmt), 1)
+    net.launch = {"path": args.path, "window_steps": args.window, "update_block": args.update_block,
+                  "update_groups": args.update_groups}
+    net.run(args.warm_steps)
+    net.run(args.run_steps)
+    torch.cuda.synchronize()
+    if dist.rank == 0:
+        print(json.dumps({"mode": "profile", "grid": args.grid, "regime": args.regime, "format": args.fmt,
+                          "launch": net.launch, "stats": net.stats()}), flush=True)
+    net.close()
+
+
 def main():
     args = parse_args()
-    if args.mode in ("batch", "serve", "grid64"):
+    if args.mode in ("batch", "serve", "grid64", "profile"):
         dist = Dist("nccl")
         try:
-            {"batch": run_batch_mode, "serve": run_serve_mode, "grid64": run_grid64_mode}[args.mode](args, dist)
+            {"batch": run_batch_mode, "serve": run_serve_mode, "grid64": run_grid64_mode,
+             "profile": run_profile_mode}[args.mode](args, dist)
         finally:
             dist.close()
         return

@@ -350,13 +350,13 @@ static int sm_count_cached() {
 
 static void default_launch(snn_net *h) {
   h->cfg.path = 0;
-  h->cfg.update_block = 256;
-  h->cfg.deliver_warps = 4;
+  h->cfg.update_block = 128;
+  h->cfg.deliver_warps = 2;
   h->cfg.fused_block = 128;
   h->cfg.fused_items_per_sm = 8;
   h->cfg.window_steps = (int32_t)h->L.window;
   h->cfg.deliver_chunk = 384;
-  h->cfg.update_groups = 2;
+  h->cfg.update_groups = 1;
 }
 
 extern "C" int snn_footprint(const snn_params *p, size_t *bytes_out) {
