@@ -415,7 +415,7 @@ static void fill_descriptor(snn_net *h) {
     d.vr[q] = h->p.V_r[q];
     d.alpha[q] = h->p.alpha_c[q];
     d.narp[q] = t.narp;
-    for (int k = 0; k < kPoisMax; ++k) d.thr[q][k] = t.thr[k];
+    for (int k = 0; k < kPoisMax; ++k) d.thr[q][k] = (uint32_t)t.thr[k];   // <= 2^20
   }
   d.V = reinterpret_cast<float *>(base + L.off_V);
   d.c = reinterpret_cast<float *>(base + L.off_c);

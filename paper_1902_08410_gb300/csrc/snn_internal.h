@@ -59,7 +59,7 @@ struct alignas(16) NetDev {
   float el[kNPop], vth[kNPop], vr[kNPop], alpha[kNPop];
   int32_t narp[kNPop];
   uint32_t pad0[2];
-  unsigned long long thr[kNPop][kPoisMax];   // Poisson CDF thresholds (u32 scale)
+  uint32_t thr[kNPop][kPoisMax];   // Poisson CDF thresholds, scaled by 2^20
 
   // --- device arrays
   float *V;             // [N_pad]

@@ -141,26 +141,87 @@ __device__ __forceinline__ uint32_t ld_na_u32(const uint32_t *p) {
 // Neuron update (Eq. 2 over one step, Poisson drive) of 4 consecutive neurons.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t poisson_count(const NetDev &nd, int pop, uint32_t w) {
-  const unsigned long long u = w >> 12;   // 20-bit uniform
+  const uint32_t u = w >> 12;   // 20-bit uniform
   uint32_t k = 0;
   while (k < (uint32_t)kPoisMax && u >= nd.thr[pop][k]) ++k;
   return k;
 }
 
-// Amplitudes of external events 1..k-1 of neuron n at step t (2^-16 mV); rare.
-__device__ __noinline__ int32_t extra_amplitudes(const NetDev &nd, int pop, uint32_t k, uint32_t n, uint32_t t) {
+// Amplitudes of external events e0..k-1 of neuron n at step t (2^-16 mV), one
+// Philox draw per 8 events; only the rare tail e0 = 9 comes through here.
+__device__ __noinline__ int32_t extra_amplitudes(const NetDev &nd, int pop, uint32_t e0, uint32_t k, uint32_t n,
+                                                 uint32_t t) {
   const int32_t *ap = nd.amp + pop * kZTab;
   int32_t I = 0;
   uint4 q = make_uint4(0, 0, 0, 0);
-  for (uint32_t e = 1; e < k; ++e) {
+  for (uint32_t e = e0; e < k; ++e) {
     const uint32_t i = (e - 1u) & 7u;
-    if (i == 0) q = philox4x32_10(n, t, 3u, (e - 1u) >> 3, nd.key0, nd.key1);
+    if (e == e0 || i == 0) q = philox4x32_10(n, t, 3u, (e - 1u) >> 3, nd.key0, nd.key1);
     const uint32_t w = i >> 1;
     const uint32_t word = (w == 0) ? q.x : ((w == 1) ? q.y : ((w == 2) ? q.z : q.w));
     const uint32_t half = (i & 1u) ? (word >> 16) : (word & 0xFFFFu);
     I += __ldg(ap + (half >> 4));
   }
   return I;
+}
+
+// Amplitudes of events 1..k-1 (k >= 2) of neuron n: events 1..8 come from the
+// halves of one draw and their table loads are independent.
+__device__ __forceinline__ int32_t extra_sum(const NetDev &nd, int pop, uint32_t k, uint32_t n, uint32_t t) {
+  const int32_t *ap = nd.amp + pop * kZTab;
+  const uint4 R = philox4x32_10(n, t, 3u, 0u, nd.key0, nd.key1);
+  const uint32_t h[8] = {R.x & 0xFFFFu, R.x >> 16, R.y & 0xFFFFu, R.y >> 16,
+                         R.z & 0xFFFFu, R.z >> 16, R.w & 0xFFFFu, R.w >> 16};
+  int32_t I = 0;
+#pragma unroll
+  for (uint32_t j = 0; j < 8u; ++j)
+    if (j + 1u < k) I += __ldg(ap + (h[j] >> 4));
+  if (k > 9u) I += extra_amplitudes(nd, pop, 9u, k, n, t);
+  return I;
+}
+
+// Events 1..k-1 of every neuron of the warp's 128-neuron tile that received
+// more than one external event this step (about 1.4% of neurons at 0.18
+// expected events).  The pending (lane, q) pairs are numbered q-major by
+// ballots and lane i serves pair i, so a warp pays one draw and one table
+// round trip instead of one per neuron and event; sums return by shuffle.
+// Called by whole warps (all 32 lanes).
+__device__ __forceinline__ void extra_events_warp(const NetDev &nd, uint32_t n0, uint32_t t, const uint32_t (&kx)[4],
+                                                  int32_t (&Iv)[4]) {
+  const uint32_t lane = lane_id(), lt = (1u << lane) - 1u;
+  uint32_t bal[4], idx[4], cnt[4], total = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    bal[q] = __ballot_sync(0xFFFFFFFFu, kx[q] > 1u);
+    idx[q] = total + __popc(bal[q] & lt);
+    cnt[q] = total;
+    total += __popc(bal[q]);
+  }
+  if (total == 0u) return;
+  const uint32_t packed = kx[0] | (kx[1] << 8) | (kx[2] << 16) | (kx[3] << 24);   // each count <= 16
+  const uint32_t tile0 = n0 - lane * 4u;
+  for (uint32_t s = 0; s < total; s += 32u) {
+    const uint32_t i = s + lane;
+    uint32_t q = 0, owner = 0;
+    if (i < total) {
+      q = (i >= cnt[1] ? 1u : 0u) + (i >= cnt[2] ? 1u : 0u) + (i >= cnt[3] ? 1u : 0u);
+      uint32_t b = (q == 0u) ? bal[0] : ((q == 1u) ? bal[1] : ((q == 2u) ? bal[2] : bal[3]));
+      const uint32_t base = (q == 0u) ? 0u : ((q == 1u) ? cnt[1] : ((q == 2u) ? cnt[2] : cnt[3]));
+      for (uint32_t r = base; r < i; ++r) b &= b - 1u;   // drop the lower set bits: rank i - base
+      owner = (uint32_t)(__ffs(b) - 1);
+    }
+    const uint32_t pk = __shfl_sync(0xFFFFFFFFu, packed, owner);
+    int32_t acc = 0;
+    if (i < total) {
+      const uint32_t n = tile0 + owner * 4u + q;
+      acc = extra_sum(nd, pop_of_local(n % (uint32_t)kK), (pk >> (8u * q)) & 0xFFu, n, t);
+    }
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) {
+      const int32_t v = __shfl_sync(0xFFFFFFFFu, acc, idx[qq] & 31u);
+      if (kx[qq] > 1u && idx[qq] - s < 32u) Iv[qq] += v;
+    }
+  }
 }
 
 __device__ __forceinline__ void red_add_u64(unsigned long long *addr, unsigned long long v) {
@@ -209,15 +270,18 @@ __device__ __forceinline__ void load_state4(const NetDev &nd, uint32_t n0, Group
   g.ref = ld_na_u32(reinterpret_cast<const uint32_t *>(nd.ref) + i4);
 }
 
+// The slot is cleared by step4 after the neuron state is stored: a store right
+// behind the load to the same address held every later load of the warp back
+// (the whole step took ~1.7x longer on a 720k-neuron grid).
 __device__ __forceinline__ void load_ring4(const NetDev &nd, uint32_t n0, uint32_t st, Group4 &g) {
-  int4 *slot = reinterpret_cast<int4 *>(nd.ring + (size_t)st * nd.N_pad) + (n0 >> 2);
-  g.I = ld_na_i4(slot);
-  *slot = make_int4(0, 0, 0, 0);
+  g.I = ld_na_i4(reinterpret_cast<const int4 *>(nd.ring + (size_t)st * nd.N_pad) + (n0 >> 2));
 }
 
-// Advance the 4 neurons of g by step t; returns the 4-bit spike mask and adds
-// the number of external events to n_ext.
-__device__ __forceinline__ uint32_t step4(const NetDev &nd, uint32_t n0, uint32_t t, Group4 &g, uint32_t &n_ext) {
+// Advance the 4 neurons of g by step t (ring slot st, read by load_ring4 and
+// cleared here); returns the 4-bit spike mask and adds the number of external
+// events to n_ext.
+__device__ __forceinline__ uint32_t step4(const NetDev &nd, uint32_t n0, uint32_t t, uint32_t st, Group4 &g,
+                                          uint32_t &n_ext) {
   // one counter-based draw serves the four neurons (word n mod 4 each)
   const uint4 R = philox4x32_10(n0 >> 2, t, 1u, 0u, nd.key0, nd.key1);
   const uint32_t Wv[4] = {R.x, R.y, R.z, R.w};
@@ -234,9 +298,7 @@ __device__ __forceinline__ uint32_t step4(const NetDev &nd, uint32_t n0, uint32_
 #pragma unroll
   for (int q = 0; q < 4; ++q)   // first external event: independent table loads
     if (kx[q]) Iv[q] += __ldg(nd.amp + pops[q] * kZTab + (Wv[q] & 0xFFFu));
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-    if (kx[q] > 1u) Iv[q] += extra_amplitudes(nd, pops[q], kx[q], n0 + q, t);
+  extra_events_warp(nd, n0, t, kx, Iv);
   float Vv[4] = {g.V.x, g.V.y, g.V.z, g.V.w};
   float cv[4] = {g.c.x, g.c.y, g.c.z, g.c.w};
   uint32_t rv[4] = {g.ref & 0xFFu, (g.ref >> 8) & 0xFFu, (g.ref >> 16) & 0xFFu, g.ref >> 24};
@@ -253,6 +315,7 @@ __device__ __forceinline__ uint32_t step4(const NetDev &nd, uint32_t n0, uint32_
     reinterpret_cast<float4 *>(nd.V)[i4] = make_float4(Vv[0], Vv[1], Vv[2], Vv[3]);
     reinterpret_cast<float4 *>(nd.c)[i4] = make_float4(cv[0], cv[1], cv[2], cv[3]);
     reinterpret_cast<uint32_t *>(nd.ref)[i4] = rv[0] | (rv[1] << 8) | (rv[2] << 16) | (rv[3] << 24);
+    reinterpret_cast<int4 *>(nd.ring + (size_t)st * nd.N_pad)[i4] = make_int4(0, 0, 0, 0);
   }
   return mask;
 }
@@ -260,8 +323,9 @@ __device__ __forceinline__ uint32_t step4(const NetDev &nd, uint32_t n0, uint32_
 __device__ __forceinline__ uint32_t update4(const NetDev &nd, uint32_t n0, uint32_t t, uint32_t &n_ext) {
   Group4 g;
   load_state4(nd, n0, g);
-  load_ring4(nd, n0, t % nd.D, g);
-  return step4(nd, n0, t, g, n_ext);
+  const uint32_t st = t % nd.D;
+  load_ring4(nd, n0, st, g);
+  return step4(nd, n0, t, st, g, n_ext);
 }
 
 // Warp-level recording of the warp's spikes over G groups (all 32 lanes
@@ -587,8 +651,11 @@ __global__ void __launch_bounds__(kBuildWarpsMax * 32) k_build_rows(NetDev nd, B
 // neuron range ((b * G + g) * BLOCK + thread) * 4, so every warp owns whole
 // aligned 128-neuron tiles.  The state loads of all groups are issued before
 // the window is read, then the ring slots once the step is known.
+// One group per thread is capped at 48 registers (40 resident warps per SM), so
+// that a 720k-neuron grid (37 warps per SM) runs in a single wave.
 template <int BLOCK, int G>
-__global__ void __launch_bounds__(BLOCK) k_update(const __grid_constant__ NetDev nd, uint32_t k) {
+__global__ void __launch_bounds__(BLOCK, G == 1 ? 1280 / BLOCK : 1) k_update(const __grid_constant__ NetDev nd,
+                                                                           uint32_t k) {
   uint32_t n0[G];
   bool live[G];
   bool any = false;
@@ -616,7 +683,7 @@ __global__ void __launch_bounds__(BLOCK) k_update(const __grid_constant__ NetDev
   for (int g = 0; g < G; ++g) {
     mask[g] = 0;
     n_ext[g] = 0;
-    if (live[g]) mask[g] = step4(nd, n0[g], t, st4[g], n_ext[g]);
+    if (live[g]) mask[g] = step4(nd, n0[g], t, slot, st4[g], n_ext[g]);
   }
   // record per group whose tile is live (warp-uniform)
   if (live[G - 1]) {
