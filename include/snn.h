@@ -108,6 +108,11 @@ typedef struct snn_launch {
                               (two-kernel path <= 1152, fused path <= 256) */
   int32_t update_groups;   /* groups of 4 neurons per update thread: 1, 2 or 4
                               (512-thread blocks: 1 or 2) */
+  int32_t l2_persist;      /* two-kernel path: 1 = the neuron state and delay ring are
+                              given a persisting L2 access-policy window (the CUDA
+                              context's persisting set-aside is raised to the device
+                              maximum while any such network lives, then restored);
+                              0 = normal caching */
 } snn_launch;
 
 typedef void *(*snn_alloc_fn)(size_t bytes, void *ctx);

@@ -102,8 +102,15 @@ struct FusedTable {
 cudaError_t prepare_kernels();
 cudaError_t launch_build_rows(const NetDev &h_nd, const BuildDev &bd, cudaStream_t s);
 cudaError_t launch_init_state(const NetDev &nd, cudaStream_t s);
-cudaError_t launch_update(const NetDev &nd, uint32_t k, int block, int groups, cudaStream_t s);
-cudaError_t launch_deliver(const NetDev &nd, uint32_t k, uint32_t chunk, int warps, int blocks, cudaStream_t s);
+// Persisting L2 access-policy window attached to a launch (bytes == 0: none).
+struct L2Window {
+  void *base = nullptr;
+  size_t bytes = 0;
+  float hit_ratio = 0.0f;
+};
+cudaError_t launch_update(const NetDev &nd, uint32_t k, int block, int groups, const L2Window &l2, cudaStream_t s);
+cudaError_t launch_deliver(const NetDev &nd, uint32_t k, uint32_t chunk, int warps, int blocks, const L2Window &l2,
+                           cudaStream_t s);
 cudaError_t launch_fused(const FusedTable &tab, uint32_t k, int block, int blocks, cudaStream_t s);
 uint32_t max_chunk_records();        // largest chunk of the two-kernel delivery
 uint32_t max_fused_chunk_records();  // largest chunk of the fused step

@@ -833,11 +833,36 @@ cudaError_t launch_build_rows(const NetDev &h_nd, const BuildDev &bd, cudaStream
   return cudaGetLastError();
 }
 
-cudaError_t launch_update(const NetDev &nd, uint32_t k, int block, int groups, cudaStream_t s) {
+// Launch with an optional persisting L2 access-policy window.
+template <typename... Args>
+static cudaError_t launch_ex(void (*kernel)(Args...), dim3 grid, dim3 block, size_t smem, const L2Window &l2,
+                             cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  unsigned n = 0;
+  if (l2.bytes) {
+    attr[n].id = cudaLaunchAttributeAccessPolicyWindow;
+    attr[n].val.accessPolicyWindow.base_ptr = l2.base;
+    attr[n].val.accessPolicyWindow.num_bytes = l2.bytes;
+    attr[n].val.accessPolicyWindow.hitRatio = l2.hit_ratio;
+    attr[n].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    attr[n].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    ++n;
+  }
+  cfg.attrs = n ? attr : nullptr;
+  cfg.numAttrs = n;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+cudaError_t launch_update(const NetDev &nd, uint32_t k, int block, int groups, const L2Window &l2, cudaStream_t s) {
   const uint32_t per_block = (uint32_t)block * 4u * (uint32_t)groups;
   const uint32_t blocks = (nd.N_pad + per_block - 1) / per_block;
 #define SNN_UPD(B, G) \
-  if (block == B && groups == G) { k_update<B, G><<<blocks, B, 0, s>>>(nd, k); return cudaGetLastError(); }
+  if (block == B && groups == G) return launch_ex(k_update<B, G>, dim3(blocks), dim3(B), 0, l2, s, nd, k);
   SNN_UPD(128, 1) SNN_UPD(128, 2) SNN_UPD(128, 4)
   SNN_UPD(256, 1) SNN_UPD(256, 2) SNN_UPD(256, 4)
   SNN_UPD(512, 1) SNN_UPD(512, 2)
@@ -845,10 +870,10 @@ cudaError_t launch_update(const NetDev &nd, uint32_t k, int block, int groups, c
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_deliver(const NetDev &nd, uint32_t k, uint32_t chunk, int warps, int blocks, cudaStream_t s) {
+cudaError_t launch_deliver(const NetDev &nd, uint32_t k, uint32_t chunk, int warps, int blocks, const L2Window &l2,
+                           cudaStream_t s) {
   if (warps < 1 || warps > 8 || chunk < 8 || chunk > kStageCap || (chunk % 8)) return cudaErrorInvalidValue;
-  k_deliver<<<blocks, warps * 32, deliver_smem_bytes(warps), s>>>(nd, k, chunk);
-  return cudaGetLastError();
+  return launch_ex(k_deliver, dim3(blocks), dim3(warps * 32), deliver_smem_bytes(warps), l2, s, nd, k, chunk);
 }
 
 cudaError_t launch_fused(const FusedTable &tab, uint32_t k, int block, int blocks, cudaStream_t s) {
