@@ -67,8 +67,12 @@ def parse_args():
     ap.add_argument("--warm-steps", type=int, default=1024)
     ap.add_argument("--run-steps", type=int, default=64)
     ap.add_argument("--window", type=int, default=64)
-    ap.add_argument("--update-block", type=int, default=128)
+    ap.add_argument("--update-block", type=int, default=256)
     ap.add_argument("--update-groups", type=int, default=1)
+    ap.add_argument("--deliver-warps", type=int, default=2)
+    ap.add_argument("--deliver-chunk", type=int, default=384)
+    ap.add_argument("--l2-persist", type=int, choices=[0, 1], default=1,
+                    help="persisting L2 window (profile mode, and grid mode with --no-tune)")
     ap.add_argument("--grid64-lambdas", type=str, default="0.4,1.0,2.0")
     ap.add_argument("--batch-nets", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=20_000)
@@ -280,12 +284,19 @@ def run_gb300(args, dist: Dist):
     if not args.no_tune:
         for n in nets:
             n.run(2000)
-            n.autotune(200)
+            n.autotune(400)
+    else:
+        for n in nets:
+            n.launch = {"l2_persist": args.l2_persist}
     steps = args.sim_steps
 
-    def bench_step():
-        for n in nets:
+    def bench_step(evs=None):
+        for i, n in enumerate(nets):
+            if evs is not None:
+                evs[i][0].record(stream)
             n.run(steps)
+            if evs is not None:
+                evs[i][1].record(stream)
 
     for _ in range(args.warmup):
         bench_step()
@@ -295,11 +306,15 @@ def run_gb300(args, dist: Dist):
     torch.cuda.synchronize()
     sampler.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    net_evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in nets] for _ in range(args.steps)]
     e0.record(stream)
-    for _ in range(args.steps):
-        bench_step()
+    for i in range(args.steps):
+        bench_step(net_evs[i])
     e1.record(stream)
     torch.cuda.synchronize()
+    # per network: ms per simulated time step over the timed region
+    net_step_ms = [sum(net_evs[i][j][0].elapsed_time(net_evs[i][j][1]) for i in range(args.steps))
+                   / (args.steps * steps) for j in range(len(nets))]
     dist.barrier()
     clocks = sampler.stop()
     elapsed = e0.elapsed_time(e1) / 1e3
@@ -314,16 +329,25 @@ def run_gb300(args, dist: Dist):
     sim_s = args.steps * steps * W.DT_MS * 1e-3
 
     # ---- roofline of the dominant kernel (CUDA events on the launching stream)
+    # A kernel's launch duration is the network's measured time per step in the
+    # timed region (graph replays, CUDA events) times the kernel's share of the
+    # step; the shares come from snn_time_kernels (the same steps captured with
+    # event nodes around every kernel: those nodes lengthen each span by a few
+    # microseconds, so only their ratio is used).  Launch gaps and window
+    # drains are charged to the kernels, so `achieved` is a lower bound.
     peak, peak_kind = measured_peaks()
     kt = []
-    for n in nets:
+    for j, n in enumerate(nets):
         s_a = n.stats()["spikes"]
         tk = n.time_kernels(200)
         spk_per_step = (n.stats()["spikes"] - s_a) / 200.0
         rec_bytes = 8 if n.params["record_format"] == W.REC_F32 else 6
         upd_bytes = 26.0 * n.N
         dl_bytes = spk_per_step * (n.M * rec_bytes + 8)
-        kt.append((tk, upd_bytes, dl_bytes))
+        sh_u = tk["update_ms"] / (tk["update_ms"] + tk["deliver_ms"])
+        tk_step = {"update_ms": net_step_ms[j] * sh_u, "deliver_ms": net_step_ms[j] * (1.0 - sh_u),
+                   "event_node_update_ms": tk["update_ms"], "event_node_deliver_ms": tk["deliver_ms"]}
+        kt.append((tk_step, upd_bytes, dl_bytes))
     upd_ms = sum(k[0]["update_ms"] for k in kt) / len(kt)
     dl_ms = sum(k[0]["deliver_ms"] for k in kt) / len(kt)
     upd_b = sum(k[1] for k in kt) / len(kt)
@@ -340,6 +364,9 @@ def run_gb300(args, dist: Dist):
     roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "peak_kind": peak_kind, "traffic": committed_traffic(dom),
                 "share_of_step": share[dom],
+                "method": "launch duration = measured ms per time step (CUDA events around each network's graph "
+                          "replays in the timed region) x the kernel's share of an event-bracketed step",
+                "step_ms": {names[j]: net_step_ms[j] for j in range(len(nets))},
                 "kernels": {k: {**v, "frac": v["achieved_gbs"] / peak, "share": share[k]} for k, v in kernels.items()}}
 
     # ---- end to end through the C ABI with host buffers
@@ -599,7 +626,8 @@ def run_profile_mode(args, dist: Dist):
     fmt = W.REC_F32 if args.fmt == "f32" else W.REC_I16
     net = snn.Network(W.base_params(args.grid, args.grid, 1.0, args.regime, record_format=fmt), 1)
     net.launch = {"path": args.path, "window_steps": args.window, "update_block": args.update_block,
-                  "update_groups": args.update_groups}
+                  "update_groups": args.update_groups, "deliver_warps": args.deliver_warps,
+                  "deliver_chunk": args.deliver_chunk, "l2_persist": args.l2_persist}
     net.run(args.warm_steps)
     net.run(args.run_steps)
     torch.cuda.synchronize()

@@ -181,11 +181,13 @@ int snn_set_launch(snn_handle h, const snn_launch *cfg);
  * restored afterwards, so results are unchanged. */
 int snn_autotune(snn_handle h, uint32_t trial_steps);
 
-/* Advance the network by `steps` steps with the two-kernel path launched
- * directly (no graph), bracketing every launch with CUDA events on the
- * network's stream.  ms_out[0] / ms_out[1] receive the mean duration of one
- * update / one delivery launch in milliseconds.  Results are identical to
- * snn_run; the call exists to measure kernels without a profiler. */
+/* Advance the network by `steps` (1..window) steps with the two-kernel path,
+ * captured into one CUDA graph as snn_run runs it, with an event record node
+ * before and after every kernel; the graph runs on the network's stream.
+ * ms_out[0] / ms_out[1] receive the mean duration of one update / one
+ * delivery launch in milliseconds (each span includes that kernel's launch
+ * inside the graph).  Results are identical to snn_run; the call exists to
+ * measure kernels without a profiler. */
 int snn_time_kernels(snn_handle h, uint32_t steps, double *ms_out);
 
 /* Build the synapse rows of a network (the same construction and the same

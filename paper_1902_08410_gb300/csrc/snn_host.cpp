@@ -416,14 +416,14 @@ static int sm_count_cached() {
 
 static void default_launch(snn_net *h) {
   h->cfg.path = 0;
-  h->cfg.update_block = 128;
+  h->cfg.update_block = 256;
   h->cfg.deliver_warps = 2;
   h->cfg.fused_block = 128;
   h->cfg.fused_items_per_sm = 8;
   h->cfg.window_steps = (int32_t)h->L.window;
   h->cfg.deliver_chunk = 384;
   h->cfg.update_groups = 1;
-  h->cfg.l2_persist = 0;
+  h->cfg.l2_persist = 1;
 }
 
 extern "C" int snn_footprint(const snn_params *p, size_t *bytes_out) {
@@ -1161,14 +1161,37 @@ extern "C" int snn_time_kernels(snn_handle h, uint32_t steps, double *ms_out) {
   L2Window l2;
   int rc0 = l2_window(h, &l2);
   if (rc0) return rc0;
-  for (uint32_t k = 0; k < steps; ++k) {
-    CU_TRY(cudaEventRecord(ev[4 * k + 0], s));
-    CU_TRY(launch_update(h->hd, k, h->cfg.update_block, h->cfg.update_groups, l2, s));
-    CU_TRY(cudaEventRecord(ev[4 * k + 1], s));
-    CU_TRY(cudaEventRecord(ev[4 * k + 2], s));
-    CU_TRY(launch_deliver(h->hd, k, (uint32_t)h->cfg.deliver_chunk, h->cfg.deliver_warps, sms * 4, l2, s));
-    CU_TRY(cudaEventRecord(ev[4 * k + 3], s));
+  // the steps are captured into one graph, as snn_run runs them, with event
+  // record nodes around every kernel
+  const NetDev d = descriptor(h, 0);
+  cudaStream_t cs = h->cap_stream;
+  CU_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  cudaError_t err = cudaSuccess;
+  for (uint32_t k = 0; k < steps && err == cudaSuccess; ++k) {
+    err = cudaEventRecordWithFlags(ev[4 * k + 0], cs, cudaEventRecordExternal);
+    if (err == cudaSuccess) err = launch_update(d, k, h->cfg.update_block, h->cfg.update_groups, l2, cs);
+    if (err == cudaSuccess) err = cudaEventRecordWithFlags(ev[4 * k + 1], cs, cudaEventRecordExternal);
+    if (err == cudaSuccess) err = cudaEventRecordWithFlags(ev[4 * k + 2], cs, cudaEventRecordExternal);
+    if (err == cudaSuccess)
+      err = launch_deliver(d, k, (uint32_t)h->cfg.deliver_chunk, h->cfg.deliver_warps, sms * 4, l2, cs);
+    if (err == cudaSuccess) err = cudaEventRecordWithFlags(ev[4 * k + 3], cs, cudaEventRecordExternal);
   }
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+  if (err != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(SNN_ERR_CUDA, std::string("timing graph capture: ") +
+                                  cudaGetErrorString(err != cudaSuccess ? err : e2));
+  }
+  cudaGraphExec_t gx = nullptr;
+  cudaError_t e3 = cudaGraphInstantiate(&gx, g, 0);
+  cudaGraphDestroy(g);
+  if (e3 != cudaSuccess) return fail(SNN_ERR_CUDA, std::string("timing graph instantiate: ") + cudaGetErrorString(e3));
+  cudaError_t e4 = cudaGraphLaunch(gx, s);
+  cudaError_t e5 = cudaStreamSynchronize(s);
+  cudaGraphExecDestroy(gx);
+  if (e4 != cudaSuccess || e5 != cudaSuccess)
+    return fail(SNN_ERR_CUDA, std::string("timing graph: ") + cudaGetErrorString(e4 != cudaSuccess ? e4 : e5));
   h->launches += 2ull * steps;
   int rc = drain_window(h, 0, t0, s);
   if (rc) return rc;
@@ -1278,10 +1301,12 @@ extern "C" int snn_autotune(snn_handle h, uint32_t trial_steps) {
   CU_TRY(cudaEventCreate(&e1));
   float best_ms = 1e30f;
   snn_launch best = orig;
-  // time one shape from the snapshot (the first pass captures the graph)
-  auto trial = [&](const snn_launch &c) -> int {
+  // time one shape from the snapshot: the first pass captures the graphs, the
+  // shape's time is the best of the next `reps` passes
+  auto trial = [&](const snn_launch &c, int reps, float *ms_out) -> int {
     h->cfg = c;
-    for (int rep = 0; rep < 2; ++rep) {
+    *ms_out = 1e30f;
+    for (int rep = 0; rep <= reps; ++rep) {
       CU_TRY(cudaMemcpyAsync(base, snap.p, state_bytes, cudaMemcpyDeviceToDevice, s));
       h->t = t_saved;
       CU_TRY(cudaEventRecord(e0, s));
@@ -1291,22 +1316,30 @@ extern "C" int snn_autotune(snn_handle h, uint32_t trial_steps) {
       CU_TRY(cudaEventSynchronize(e1));
       float ms = 0;
       CU_TRY(cudaEventElapsedTime(&ms, e0, e1));
-      if (rep == 1 && ms < best_ms) {
-        best_ms = ms;
-        best = c;
-      }
+      if (rep > 0) *ms_out = std::min(*ms_out, ms);
     }
     return SNN_OK;
   };
   int status = SNN_OK;
   for (const snn_launch &c : cands) {
-    status = trial(c);
+    float ms = 0;
+    status = trial(c, 1, &ms);
     if (status != SNN_OK) break;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
   }
-  if (status == SNN_OK && best.path == 0) {   // then the L2 residency switch on the best shape
-    snn_launch c = best;
-    c.l2_persist = 1 - c.l2_persist;
-    status = trial(c);
+  if (status == SNN_OK && best.path == 0) {
+    // the L2 residency switch on the best shape: both settings timed again,
+    // and the persisting window is dropped only when that is clearly faster
+    snn_launch on = best, off = best;
+    on.l2_persist = 1;
+    off.l2_persist = 0;
+    float ms_on = 0, ms_off = 0;
+    status = trial(on, 3, &ms_on);
+    if (status == SNN_OK) status = trial(off, 3, &ms_off);
+    if (status == SNN_OK) best = (ms_off < 0.97f * ms_on) ? off : on;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

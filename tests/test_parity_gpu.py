@@ -212,6 +212,13 @@ def test_launch_shapes_and_autotune_keep_results(snn, oracle_mod):
     g.autotune(50)
     g.run(500)
     _assert_same_run(g, o, 700)
+    # kernel timing (a captured graph with event nodes) advances like a run
+    g = snn.Network(p, 21)
+    g.run(150)
+    tk = g.time_kernels(100)
+    assert tk["update_ms"] > 0 and tk["deliver_ms"] > 0
+    g.run(450)
+    _assert_same_run(g, o, 700)
 
 
 # ---------------------------------------------------------------------------
