@@ -117,6 +117,14 @@ class Dist:
             self.pg.destroy_process_group()
 
 
+def job_throughput(dist: Dist, units_local: float, seconds_local: float) -> tuple[float, float]:
+    """Whole-job throughput of independent replicas: the units of all ranks over
+    the slowest rank's time.  Returns (throughput, slowest time)."""
+    t_max = dist.reduce(seconds_local, "max")
+    units_all = dist.reduce(float(units_local), "sum")
+    return units_all / t_max, t_max
+
+
 # ---------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
@@ -323,9 +331,7 @@ def run_gb300(args, dist: Dist):
     ext = [b["ext_events"] - a["ext_events"] for a, b in zip(st0, st1)]
     launches = sum(b["kernel_launches"] - a["kernel_launches"] for a, b in zip(st0, st1))
     events_local = sum(spikes) * EQUIV_PER_SPIKE
-    t_max = dist.reduce(elapsed, "max")
-    events_all = dist.reduce(float(events_local), "sum")
-    value = events_all / t_max
+    value, t_max = job_throughput(dist, events_local, elapsed)
     sim_s = args.steps * steps * W.DT_MS * 1e-3
 
     # ---- roofline of the dominant kernel (CUDA events on the launching stream)
@@ -389,9 +395,8 @@ def run_gb300(args, dist: Dist):
             ev += s["spikes"] * EQUIV_PER_SPIKE
             n.close()
         torch.cuda.synchronize()
-        t_e2e = dist.reduce(time.perf_counter() - t0, "max")
-        ev_all = dist.reduce(float(ev), "sum")
-        e2e = {"value": ev_all / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+        e2e_value, t_e2e = job_throughput(dist, ev, time.perf_counter() - t0)
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "step": "build both 24x24 networks from host parameters, 0.5 s simulated each, read spikes "
                        "and rates into host arrays, free", "seconds_per_step": t_e2e}
 
@@ -474,9 +479,9 @@ def run_batch_mode(args, dist: Dist):
         bs, bi = bn.spikes(0, args.plain_steps)
         same += int(np.array_equal(ps, bs) and np.array_equal(pi, bi))
         n.close()
-    t_b = dist.reduce(t_batch, "max")
+    batch_value, _ = job_throughput(dist, ev_batch, t_batch)
     line = {
-        "metric": METRIC, "mode": "batch", "value": dist.reduce(float(ev_batch), "sum") / t_b, "unit": UNIT,
+        "metric": METRIC, "mode": "batch", "value": batch_value, "unit": UNIT,
         "n_gpus": dist.world, "higher_is_better": True, "data": "synthetic", "dtype": "f32+i32",
         "config": {"workload": f"{len(nets)} networks, sides U{{2..8}}, g_c on a 16-point SWA->AW grid, "
                                f"nu_ext U[2, 8] Hz, i16 records, {args.batch_steps} steps each",
