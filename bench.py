@@ -9,6 +9,10 @@ library's public API.  Events follow the paper's equivalent-event count
 (Sec. 2.4): every spike counts its recurrent plus external synapses (1125 +
 400).
 
+The two networks run concurrently, each on its own CUDA stream
+(`run_concurrent`: their kernels overlap on the GPU); `--sequential` runs them
+one after the other.
+
 The JSON line reports the device-resident throughput (`value`), an end-to-end
 number through the C ABI with host buffers (`e2e`), the roofline of the
 dominant kernel measured with CUDA events, SM clocks sampled during the timed
@@ -53,6 +57,8 @@ def parse_args():
     ap.add_argument("--sim-steps", type=int, default=STEPS_PER_BENCH_STEP,
                     help="0.1 ms steps per network per bench step")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--sequential", action="store_true",
+                    help="run the two networks one after the other instead of concurrently")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--mode", choices=["grid", "batch", "serve", "grid64", "profile"], default="grid",
@@ -284,10 +290,12 @@ def run_gb300(args, dist: Dist):
     snn.lib()
     stream = torch.cuda.current_stream()
 
-    nets, names = [], []
+    # every network on its own stream: snn_run_concurrent overlaps their kernels
+    nets, names, streams = [], [], []
     for reg in ("SWA", "AW"):
         wl = W.grid_24x24(reg)
-        nets.append(snn.Network(wl["params"], wl["seed"] + 7919 * dist.rank))
+        streams.append(torch.cuda.Stream())
+        nets.append(snn.Network(wl["params"], wl["seed"] + 7919 * dist.rank, stream=streams[-1].cuda_stream))
         names.append(reg)
     if not args.no_tune:
         for n in nets:
@@ -298,13 +306,12 @@ def run_gb300(args, dist: Dist):
             n.launch = {"l2_persist": args.l2_persist}
     steps = args.sim_steps
 
-    def bench_step(evs=None):
-        for i, n in enumerate(nets):
-            if evs is not None:
-                evs[i][0].record(stream)
-            n.run(steps)
-            if evs is not None:
-                evs[i][1].record(stream)
+    def bench_step():
+        if args.sequential:
+            for n in nets:
+                n.run(steps)
+        else:
+            snn.run_concurrent(nets, steps)
 
     for _ in range(args.warmup):
         bench_step()
@@ -313,16 +320,18 @@ def run_gb300(args, dist: Dist):
     dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
+    # device-side timing: e0 on the current stream, which the networks' streams
+    # wait for; at the end the current stream waits for both and records e1
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    net_evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in nets] for _ in range(args.steps)]
     e0.record(stream)
+    for st in streams:
+        st.wait_event(e0)
     for i in range(args.steps):
-        bench_step(net_evs[i])
+        bench_step()
+    for st in streams:
+        stream.wait_stream(st)
     e1.record(stream)
     torch.cuda.synchronize()
-    # per network: ms per simulated time step over the timed region
-    net_step_ms = [sum(net_evs[i][j][0].elapsed_time(net_evs[i][j][1]) for i in range(args.steps))
-                   / (args.steps * steps) for j in range(len(nets))]
     dist.barrier()
     clocks = sampler.stop()
     elapsed = e0.elapsed_time(e1) / 1e3
@@ -335,13 +344,23 @@ def run_gb300(args, dist: Dist):
     sim_s = args.steps * steps * W.DT_MS * 1e-3
 
     # ---- roofline of the dominant kernel (CUDA events on the launching stream)
-    # A kernel's launch duration is the network's measured time per step in the
-    # timed region (graph replays, CUDA events) times the kernel's share of the
-    # step; the shares come from snn_time_kernels (the same steps captured with
-    # event nodes around every kernel: those nodes lengthen each span by a few
-    # microseconds, so only their ratio is used).  Launch gaps and window
-    # drains are charged to the kernels, so `achieved` is a lower bound.
+    # A kernel's launch duration is the network's time per step when it runs
+    # alone (graph replays timed with CUDA events on its stream) times the
+    # kernel's share of the step; the shares come from snn_time_kernels (the
+    # same steps captured with event nodes around every kernel: those nodes
+    # lengthen each span by a few microseconds, so only their ratio is used).
+    # Launch gaps and window drains are charged to the kernels, so `achieved`
+    # is a lower bound.
     peak, peak_kind = measured_peaks()
+    solo_steps = 10 * max(1, min(n.launch["window_steps"] for n in nets))
+    net_step_ms = []
+    for j, n in enumerate(nets):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(streams[j])
+        n.run(solo_steps)
+        b.record(streams[j])
+        b.synchronize()
+        net_step_ms.append(a.elapsed_time(b) / solo_steps)
     kt = []
     for j, n in enumerate(nets):
         s_a = n.stats()["spikes"]
@@ -370,8 +389,8 @@ def run_gb300(args, dist: Dist):
     roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "peak_kind": peak_kind, "traffic": committed_traffic(dom),
                 "share_of_step": share[dom],
-                "method": "launch duration = measured ms per time step (CUDA events around each network's graph "
-                          "replays in the timed region) x the kernel's share of an event-bracketed step",
+                "method": "launch duration = ms per time step of the network run alone (CUDA events around its "
+                          "graph replays) x the kernel's share of an event-bracketed step",
                 "step_ms": {names[j]: net_step_ms[j] for j in range(len(nets))},
                 "kernels": {k: {**v, "frac": v["achieved_gbs"] / peak, "share": share[k]} for k, v in kernels.items()}}
 
@@ -383,10 +402,17 @@ def run_gb300(args, dist: Dist):
         ev = 0
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for reg in ("SWA", "AW"):
+        e2e_nets = []
+        for j, reg in enumerate(("SWA", "AW")):
             wl = W.grid_24x24(reg)
-            n = snn.Network(wl["params"], wl["seed"] + 104729 + 7919 * dist.rank)
-            n.run(e2e_steps)
+            e2e_nets.append(snn.Network(wl["params"], wl["seed"] + 104729 + 7919 * dist.rank,
+                                        stream=streams[j].cuda_stream))
+        if args.sequential:
+            for n in e2e_nets:
+                n.run(e2e_steps)
+        else:
+            snn.run_concurrent(e2e_nets, e2e_steps)
+        for n in e2e_nets:
             st_, ids = n.spikes()
             rates = n.rates()
             s = n.stats()
@@ -420,7 +446,9 @@ def run_gb300(args, dist: Dist):
                        "sim_seconds_per_step_per_network": steps * W.DT_MS * 1e-3,
                        "l2": "inputs larger than L2 (2 x 6.5 GB synapse records); the neuron state and delay ring "
                              "of each network (~67 MB) stay in L2 across time steps by design",
-                       "launch": [n.launch for n in nets], "parallelism": f"replicas x{dist.world}"},
+                       "launch": [n.launch for n in nets], "parallelism": f"replicas x{dist.world}",
+                       "networks_run": "one after the other" if args.sequential
+                       else "concurrently, one CUDA stream each (snn_run_concurrent)"},
             "sim_seconds_per_wall_second": sim_s * len(nets) * dist.world / t_max,
             "per_regime": {names[i]: {"spikes": spikes[i], "rate_hz": spikes[i] / (nets[i].N * sim_s),
                                       "recurrent_events": spikes[i] * W.OUT_DEGREE, "external_events": ext[i]}

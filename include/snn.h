@@ -151,6 +151,15 @@ int snn_run(snn_handle h, uint64_t steps);
  * share one device; the call is ordered on the first network's stream. */
 int snn_run_batch(const snn_handle *hs, const uint64_t *steps, int32_t n);
 
+/* Advance n networks by steps[i] each on the two-kernel path (launch path 0
+ * for all of them, else SNN_ERR_ARG), every network on its own stream: the
+ * windows of the networks are issued round robin, so kernels of different
+ * networks run at the same time when their streams differ (networks sharing a
+ * stream run one after the other).  Each network's results
+ * are identical to snn_run on it alone.  Returns after all steps completed and
+ * their records reached host memory.  n in 1..1024. */
+int snn_run_concurrent(const snn_handle *hs, const uint64_t *steps, int32_t n);
+
 /* Spikes with t0 <= step < t1, ordered by (step, id), as two parallel host
  * arrays of capacity `cap`.  *n_out receives the count; if it exceeds cap
  * nothing is written and SNN_ERR_BUFFER is returned. */

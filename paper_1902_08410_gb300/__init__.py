@@ -223,6 +223,17 @@ class Network:
         _check(self._lib.snn_debug_set_wait_limit(self._h, int(iterations)))
 
 
+def run_concurrent(nets, steps) -> None:
+    """Advance several networks on the two-kernel path, each on its own stream,
+    with their kernels overlapping on the GPU (see snn_run_concurrent)."""
+    nets = list(nets)
+    if isinstance(steps, int):
+        steps = [steps] * len(nets)
+    hs = (ctypes.c_void_p * len(nets))(*[n.handle.value for n in nets])
+    st = (ctypes.c_uint64 * len(nets))(*[int(s) for s in steps])
+    _check(lib().snn_run_concurrent(hs, st, len(nets)))
+
+
 def run_batch(nets, steps) -> None:
     """Advance several networks together with one fused kernel per time step."""
     nets = list(nets)

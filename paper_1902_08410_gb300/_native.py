@@ -105,7 +105,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 EXPORTS = ["snn_set_allocator", "snn_footprint", "snn_build_network", "snn_run", "snn_run_batch",
            "snn_read_spikes", "snn_rates", "snn_read_state", "snn_read_row", "snn_get_stats",
            "snn_get_launch", "snn_set_launch", "snn_autotune", "snn_free", "snn_last_error",
-           "snn_debug_set_wait_limit", "snn_time_kernels", "snn_build_rows_static"]
+           "snn_debug_set_wait_limit", "snn_time_kernels", "snn_build_rows_static", "snn_run_concurrent"]
 
 _lib = None
 
@@ -128,6 +128,7 @@ def load(build_if_needed: bool = True):
         "snn_build_network": ([P(SnnParams), u64, vp, P(vp)], ctypes.c_int),
         "snn_run": ([vp, u64], ctypes.c_int),
         "snn_run_batch": ([P(vp), P(u64), i32], ctypes.c_int),
+        "snn_run_concurrent": ([P(vp), P(u64), i32], ctypes.c_int),
         "snn_read_spikes": ([vp, u64, u64, vp, vp, sz, P(sz)], ctypes.c_int),
         "snn_rates": ([vp, vp, sz, P(sz)], ctypes.c_int),
         "snn_read_state": ([vp, vp, vp, vp, sz], ctypes.c_int),

@@ -187,6 +187,32 @@ def test_batch_matches_oracle(snn, oracle_mod):
 
 
 # ---------------------------------------------------------------------------
+# concurrent two-kernel runs on several streams
+# ---------------------------------------------------------------------------
+def test_run_concurrent_matches_oracle(snn, oracle_mod):
+    import torch
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    cases = [(W.base_params(3, 3, 0.4, "SWA"), 21, s1, 600, {}),
+             (W.base_params(2, 3, 1.0, "AW", record_format=W.REC_I16), 5, s2, 450, {"window_steps": 100}),
+             (W.base_params(2, 2, 1.0, "AW"), 9, s2, 300, {"l2_persist": 0, "window_steps": 64})]
+    nets = []
+    for p, seed, st, _, launch in cases:
+        g = snn.Network(p, seed, stream=st.cuda_stream)
+        g.launch = launch
+        nets.append(g)
+    first = [c[3] // 3 for c in cases]
+    snn.run_concurrent(nets, first)
+    snn.run_concurrent(nets, [c[3] - f for c, f in zip(cases, first)])
+    for g, (p, seed, _, steps, _) in zip(nets, cases):
+        _assert_same_run(g, _oracle(oracle_mod, p, seed, steps), steps)
+        g.close()
+    g = snn.Network(W.base_params(2, 2, 1.0, "AW"), 3)
+    g.launch = {"path": 1}
+    with pytest.raises(snn.SnnError):
+        snn.run_concurrent([g], [10])
+
+
+# ---------------------------------------------------------------------------
 # launch shapes and the tuner never change results
 # ---------------------------------------------------------------------------
 def test_launch_shapes_and_autotune_keep_results(snn, oracle_mod):
