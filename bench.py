@@ -57,6 +57,8 @@ def parse_args():
     ap.add_argument("--sim-steps", type=int, default=STEPS_PER_BENCH_STEP,
                     help="0.1 ms steps per network per bench step")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--launch", type=str, default="{}",
+                    help="grid mode with --no-tune: launch fields as JSON, e.g. '{\"deliver_blocks\": 8}'")
     ap.add_argument("--sequential", action="store_true",
                     help="run the two networks one after the other instead of concurrently")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -75,8 +77,9 @@ def parse_args():
     ap.add_argument("--window", type=int, default=64)
     ap.add_argument("--update-block", type=int, default=256)
     ap.add_argument("--update-groups", type=int, default=1)
-    ap.add_argument("--deliver-warps", type=int, default=2)
-    ap.add_argument("--deliver-chunk", type=int, default=384)
+    ap.add_argument("--deliver-warps", type=int, default=4)
+    ap.add_argument("--deliver-chunk", type=int, default=192)
+    ap.add_argument("--deliver-blocks", type=int, default=8)
     ap.add_argument("--l2-persist", type=int, choices=[0, 1], default=1,
                     help="persisting L2 window (profile mode, and grid mode with --no-tune)")
     ap.add_argument("--grid64-lambdas", type=str, default="0.4,1.0,2.0")
@@ -303,7 +306,7 @@ def run_gb300(args, dist: Dist):
             n.autotune(400)
     else:
         for n in nets:
-            n.launch = {"l2_persist": args.l2_persist}
+            n.launch = {"l2_persist": args.l2_persist, **json.loads(args.launch)}
     steps = args.sim_steps
 
     def bench_step():
@@ -344,33 +347,25 @@ def run_gb300(args, dist: Dist):
     sim_s = args.steps * steps * W.DT_MS * 1e-3
 
     # ---- roofline of the dominant kernel (CUDA events on the launching stream)
-    # A kernel's launch duration is the network's time per step when it runs
-    # alone (graph replays timed with CUDA events on its stream) times the
-    # kernel's share of the step; the shares come from snn_time_kernels (the
-    # same steps captured with event nodes around every kernel: those nodes
-    # lengthen each span by a few microseconds, so only their ratio is used).
-    # Launch gaps and window drains are charged to the kernels, so `achieved`
-    # is a lower bound.
+    # snn_time_kernels runs the next steps twice from the same state: as a plain
+    # graph (step time, CUDA events on the network's stream) and with event
+    # nodes around every kernel (the kernels' shares of the step: event nodes
+    # lengthen each span, so only their ratio is used).  A kernel's launch
+    # duration = step time x its share, both from the same steps, so launch
+    # gaps are charged to the kernels and `achieved` is a lower bound.
     peak, peak_kind = measured_peaks()
-    solo_steps = 10 * max(1, min(n.launch["window_steps"] for n in nets))
-    net_step_ms = []
+    kt, net_step_ms = [], []
     for j, n in enumerate(nets):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(streams[j])
-        n.run(solo_steps)
-        b.record(streams[j])
-        b.synchronize()
-        net_step_ms.append(a.elapsed_time(b) / solo_steps)
-    kt = []
-    for j, n in enumerate(nets):
+        tk_steps = max(1, min(351, n.launch["window_steps"]))
         s_a = n.stats()["spikes"]
-        tk = n.time_kernels(200)
-        spk_per_step = (n.stats()["spikes"] - s_a) / 200.0
+        tk = n.time_kernels(tk_steps)
+        spk_per_step = (n.stats()["spikes"] - s_a) / float(tk_steps)
         rec_bytes = 8 if n.params["record_format"] == W.REC_F32 else 6
         upd_bytes = 26.0 * n.N
         dl_bytes = spk_per_step * (n.M * rec_bytes + 8)
         sh_u = tk["update_ms"] / (tk["update_ms"] + tk["deliver_ms"])
-        tk_step = {"update_ms": net_step_ms[j] * sh_u, "deliver_ms": net_step_ms[j] * (1.0 - sh_u),
+        net_step_ms.append(tk["step_ms"])
+        tk_step = {"update_ms": tk["step_ms"] * sh_u, "deliver_ms": tk["step_ms"] * (1.0 - sh_u),
                    "event_node_update_ms": tk["update_ms"], "event_node_deliver_ms": tk["deliver_ms"]}
         kt.append((tk_step, upd_bytes, dl_bytes))
     upd_ms = sum(k[0]["update_ms"] for k in kt) / len(kt)
@@ -389,8 +384,9 @@ def run_gb300(args, dist: Dist):
     roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "peak_kind": peak_kind, "traffic": committed_traffic(dom),
                 "share_of_step": share[dom],
-                "method": "launch duration = ms per time step of the network run alone (CUDA events around its "
-                          "graph replays) x the kernel's share of an event-bracketed step",
+                "method": "launch duration = ms per time step of the network alone (the next 351 steps as a "
+                          "graph, CUDA events) x the kernel's share of the same steps run again with event nodes",
+
                 "step_ms": {names[j]: net_step_ms[j] for j in range(len(nets))},
                 "kernels": {k: {**v, "frac": v["achieved_gbs"] / peak, "share": share[k]} for k, v in kernels.items()}}
 
@@ -660,7 +656,8 @@ def run_profile_mode(args, dist: Dist):
     net = snn.Network(W.base_params(args.grid, args.grid, 1.0, args.regime, record_format=fmt), 1)
     net.launch = {"path": args.path, "window_steps": args.window, "update_block": args.update_block,
                   "update_groups": args.update_groups, "deliver_warps": args.deliver_warps,
-                  "deliver_chunk": args.deliver_chunk, "l2_persist": args.l2_persist}
+                  "deliver_chunk": args.deliver_chunk, "l2_persist": args.l2_persist,
+                  "deliver_blocks": args.deliver_blocks}
     net.run(args.warm_steps)
     net.run(args.run_steps)
     torch.cuda.synchronize()

@@ -113,6 +113,9 @@ typedef struct snn_launch {
                               context's persisting set-aside is raised to the device
                               maximum while any such network lives, then restored);
                               0 = normal caching */
+  int32_t deliver_blocks;  /* deliver blocks per SM: 1..32 (the grid is SMs x deliver_blocks;
+                              each warp stages 2 x deliver_chunk records in shared memory,
+                              at most 200 KB per block) */
 } snn_launch;
 
 typedef void *(*snn_alloc_fn)(size_t bytes, void *ctx);
@@ -190,13 +193,16 @@ int snn_set_launch(snn_handle h, const snn_launch *cfg);
  * restored afterwards, so results are unchanged. */
 int snn_autotune(snn_handle h, uint32_t trial_steps);
 
-/* Advance the network by `steps` (1..window) steps with the two-kernel path,
- * captured into one CUDA graph as snn_run runs it, with an event record node
- * before and after every kernel; the graph runs on the network's stream.
- * ms_out[0] / ms_out[1] receive the mean duration of one update / one
- * delivery launch in milliseconds (each span includes that kernel's launch
- * inside the graph).  Results are identical to snn_run; the call exists to
- * measure kernels without a profiler. */
+/* Measure the two-kernel path on the next `steps` (1..window) steps, then
+ * advance the network by them.  The steps run twice from the same state on the
+ * network's stream: once captured into one CUDA graph as snn_run runs them
+ * (ms_out[2] = mean time per step in milliseconds, CUDA events around the
+ * graph; the state is then restored from a device snapshot), and once with an
+ * event record node before and after every kernel (ms_out[0] / ms_out[1] =
+ * mean span of one update / one delivery launch; event nodes lengthen each
+ * span, so their ratio is the reliable part).  ms_out holds 3 doubles.
+ * Results are identical to snn_run; the call exists to measure kernels without
+ * a profiler.  Allocates a temporary copy of the neuron state and ring. */
 int snn_time_kernels(snn_handle h, uint32_t steps, double *ms_out);
 
 /* Build the synapse rows of a network (the same construction and the same

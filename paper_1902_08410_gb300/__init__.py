@@ -213,11 +213,12 @@ class Network:
         return self.launch
 
     def time_kernels(self, steps: int) -> dict:
-        """Mean per-launch durations (ms) of the update and delivery kernels over
-        `steps` directly launched steps, measured with CUDA events."""
-        out = (ctypes.c_double * 2)()
+        """Time the next `steps` steps (see snn_time_kernels): event-bracketed
+        spans of the update and delivery launches, and the step time of the same
+        steps as a plain graph (ms); the network advances by `steps`."""
+        out = (ctypes.c_double * 3)()
         _check(self._lib.snn_time_kernels(self._h, int(steps), out))
-        return {"update_ms": out[0], "deliver_ms": out[1]}
+        return {"update_ms": out[0], "deliver_ms": out[1], "step_ms": out[2]}
 
     def set_wait_limit(self, iterations: int) -> None:
         _check(self._lib.snn_debug_set_wait_limit(self._h, int(iterations)))

@@ -719,8 +719,8 @@ __global__ void __launch_bounds__(256) k_deliver(const __grid_constant__ NetDev 
   const uint32_t warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const uint32_t gwarp = blockIdx.x * nw + warp, total = gridDim.x * nw;
   if (gwarp >= n_items) return;
-  WarpStage ws;
-  init_stage(ws, smem + (size_t)warp * 2u * kStageCap * 8u, s_bars + 2 * warp, kStageCap);
+  WarpStage ws;   // two staging buffers of `chunk` records per warp
+  init_stage(ws, smem + (size_t)warp * 2u * chunk * 8u, s_bars + 2 * warp, chunk);
   const unsigned long long *ent = nd.rec_entries + base;
   deliver_items(nd, ws, chunk, gwarp, total, n_items, t % nd.D,
                 [&](uint32_t s) { return (uint32_t)(ent[s] & 0xFFFFFFFFull); });
@@ -800,12 +800,12 @@ int device_sm_count() {
   return sms;
 }
 
-static size_t deliver_smem_bytes(int warps) { return (size_t)warps * 2u * kStageCap * 8u; }
+static size_t deliver_smem_bytes(int warps, uint32_t chunk) { return (size_t)warps * 2u * chunk * 8u; }
 static size_t fused_smem_bytes(int block) { return (size_t)block * 16u + (size_t)(block / 32) * 2u * kFusedCap * 8u; }
 
 cudaError_t prepare_kernels() {
   cudaError_t e = cudaFuncSetAttribute(k_deliver, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)deliver_smem_bytes(8));
+                                       (int)deliver_smem_bytes(8, kStageCap));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem_bytes(512));
   if (e != cudaSuccess) return e;
@@ -873,7 +873,7 @@ cudaError_t launch_update(const NetDev &nd, uint32_t k, int block, int groups, c
 cudaError_t launch_deliver(const NetDev &nd, uint32_t k, uint32_t chunk, int warps, int blocks, const L2Window &l2,
                            cudaStream_t s) {
   if (warps < 1 || warps > 8 || chunk < 8 || chunk > kStageCap || (chunk % 8)) return cudaErrorInvalidValue;
-  return launch_ex(k_deliver, dim3(blocks), dim3(warps * 32), deliver_smem_bytes(warps), l2, s, nd, k, chunk);
+  return launch_ex(k_deliver, dim3(blocks), dim3(warps * 32), deliver_smem_bytes(warps, chunk), l2, s, nd, k, chunk);
 }
 
 cudaError_t launch_fused(const FusedTable &tab, uint32_t k, int block, int blocks, cudaStream_t s) {

@@ -224,6 +224,10 @@ def test_launch_shapes_and_autotune_keep_results(snn, oracle_mod):
               dict(path=0, update_block=128, update_groups=4, deliver_warps=4, window_steps=384, deliver_chunk=384),
               dict(path=0, update_block=256, update_groups=1, deliver_warps=2, window_steps=128, deliver_chunk=384,
                    l2_persist=1),
+              dict(path=0, update_block=256, update_groups=1, deliver_warps=4, window_steps=90, deliver_chunk=192,
+                   deliver_blocks=16),
+              dict(path=0, update_block=128, update_groups=2, deliver_warps=8, window_steps=70, deliver_chunk=16,
+                   deliver_blocks=1, l2_persist=0),
               dict(path=1, fused_block=128, fused_items_per_sm=1, window_steps=64, deliver_chunk=256),
               dict(path=1, fused_block=512, fused_items_per_sm=4, window_steps=128, deliver_chunk=96),
               dict(path=1, fused_block=128, fused_items_per_sm=16, window_steps=300, deliver_chunk=1152)]
