@@ -68,6 +68,11 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
+// Fire-and-forget prefetch of [src, src + bytes) into L2 (16-byte aligned
+// address, size a multiple of 16).
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ uint64_t l2_evict_first_policy() {
   uint64_t pol;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
@@ -374,6 +379,8 @@ __device__ __forceinline__ void record_warp(const NetDev &nd, const uint32_t (&m
     for (int q = 0; q < 4; ++q) {
       if ((mask[g] >> q) & 1u) {
         const uint32_t id = n0[g] + q;
+        // the delivery reads this row next: start fetching it into L2 now
+        bulk_prefetch_l2(nd.rows + (size_t)id * nd.row_bytes, nd.row_bytes);
         if (gbase + pos < nd.rec_cap) nd.rec_entries[gbase + pos] = tag | id;
         if (smem_list) smem_list[sbase + pos] = id;
         const uint32_t m = id / (uint32_t)kK;
