@@ -604,8 +604,8 @@ def run_grid64_mode(args, dist: Dist):
                 net = snn.Network(wl["params"], wl["seed"])
                 torch.cuda.synchronize()
                 build_s = time.perf_counter() - t0
-                net.run(2000)
-                cfg = net.autotune(100)
+                net.run(5000)              # past the initial transient, where the tuner's choice would not hold
+                cfg = net.autotune(300)
                 st0 = net.stats()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()

@@ -392,7 +392,10 @@ static void l2_release(snn_net *h) {
   }
 }
 
-// Bytes of the window over V, c, ref and the ring (the start of the arena).
+// Bytes of the persisting window at the start of the arena: V, c, ref and the
+// ring when they fit the set-aside together (the ring then stays in L2 for the
+// scattered reductions), else V, c and ref alone (a ring larger than L2
+// misses on most reductions whatever its policy; the neuron state still fits).
 static size_t l2_window_bytes(const snn_net *h) {
   int dev = 0, max_win = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -400,7 +403,8 @@ static size_t l2_window_bytes(const snn_net *h) {
     cudaGetLastError();
     return 0;
   }
-  return std::min<size_t>(h->L.off_rows, (size_t)max_win);
+  const size_t all = h->L.off_rows, state = h->L.off_ring;
+  return std::min<size_t>(all <= g_l2_setaside ? all : state, (size_t)max_win);
 }
 
 // The persisting window of network h.  Networks that run at the same time
