@@ -256,6 +256,63 @@ def oracle_sample(regimes=("SWA", "AW"), warm_steps=30, timed_steps=100, nets=No
     return events, secs, nets
 
 
+def _oracle_core_worker(spec: dict, warm_steps: int, seconds: float, barrier, out) -> None:
+    """One host core: one oracle network of the sweep, `warm_steps` untimed
+    steps, then 100-step chunks until `seconds` have passed."""
+    sys.path.insert(0, ROOT)
+    import oracle
+    o = oracle.OracleNet(spec["params"], spec["seed"])
+    o.run(warm_steps)
+    barrier.wait(timeout=900)
+    s0 = o.counters()["spikes"]
+    steps = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        o.run(100)
+        steps += 100
+    sec = time.perf_counter() - t0
+    out.put(((o.counters()["spikes"] - s0) * EQUIV_PER_SPIKE, sec, steps))
+    o.close()
+
+
+def oracle_all_cores(specs: list[dict], warm_steps: int = 100, seconds: float = 10.0) -> dict | None:
+    """The oracle on every host core at once (spawned processes, one independent
+    network of `specs` each, started together): aggregate events/s, or None if
+    a worker failed."""
+    import multiprocessing as mp
+    import queue
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")   # never fork a process that has a CUDA context
+    barrier = ctx.Barrier(cores)
+    out = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_core_worker, args=(specs[i % len(specs)], warm_steps, seconds, barrier, out))
+             for i in range(cores)]
+    for p in procs:
+        p.start()
+    res = []
+    deadline = time.time() + seconds + 900
+    while len(res) < len(procs):
+        try:
+            res.append(out.get(timeout=5))
+        except queue.Empty:
+            if any(p.exitcode not in (None, 0) for p in procs) or time.time() > deadline:
+                for p in procs:   # our own children, by handle
+                    if p.is_alive():
+                        p.terminate()
+                return None
+    for p in procs:
+        p.join(timeout=60)
+    ev = sum(r[0] for r in res)
+    wall = max(r[1] for r in res)
+    return {"value": ev / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"oracle (plain C) on all {cores} host cores at once, one independent network of the sweep "
+                      f"per core (networks 0..{min(cores, len(specs)) - 1}), {warm_steps} untimed steps, then "
+                      f"~{seconds:.0f} s of 100-step chunks each; value = all cores' events / the slowest core's time",
+            "steps_per_core": [r[2] for r in res]}
+
+
 def run_reference(args, dist: Dist):
     if dist.rank != 0:
         return
@@ -504,6 +561,9 @@ def run_batch_mode(args, dist: Dist):
         same += int(np.array_equal(ps, bs) and np.array_equal(pi, bi))
         n.close()
     batch_value, _ = job_throughput(dist, ev_batch, t_batch)
+    cpu = None
+    if not args.no_cpu_baseline and dist.world == 1:
+        cpu = oracle_all_cores(specs)
     line = {
         "metric": METRIC, "mode": "batch", "value": batch_value, "unit": UNIT,
         "n_gpus": dist.world, "higher_is_better": True, "data": "synthetic", "dtype": "f32+i32",
@@ -516,6 +576,7 @@ def run_batch_mode(args, dist: Dist):
                                    "steps": args.plain_steps},
         "speedup": (ev_batch / t_batch) / (ev_plain / t_plain),
         "identical_rasters": f"{same}/{len(nets)} networks (first {args.plain_steps} steps)",
+        "cpu_baseline": cpu,
         "build_seconds": build_s, "clocks": clocks,
     }
     for n in nets:
