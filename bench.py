@@ -75,7 +75,7 @@ def parse_args():
     ap.add_argument("--warm-steps", type=int, default=1024)
     ap.add_argument("--run-steps", type=int, default=64)
     ap.add_argument("--window", type=int, default=64)
-    ap.add_argument("--update-block", type=int, default=256)
+    ap.add_argument("--update-block", type=int, default=128)
     ap.add_argument("--update-groups", type=int, default=1)
     ap.add_argument("--deliver-warps", type=int, default=4)
     ap.add_argument("--deliver-chunk", type=int, default=192)

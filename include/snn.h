@@ -99,7 +99,7 @@ typedef struct snn_stats {
 /* Launch shapes; chosen by snn_autotune or set explicitly. */
 typedef struct snn_launch {
   int32_t path;            /* 0 = two kernels per step (update, deliver); 1 = fused step kernel */
-  int32_t update_block;    /* threads per update block: 128, 256 or 512 */
+  int32_t update_block;    /* threads per update block: 64 (update_groups 1 only), 128, 256 or 512 */
   int32_t deliver_warps;   /* warps per deliver block: 1..8 */
   int32_t fused_block;     /* threads per fused-step block: 128..512 */
   int32_t fused_items_per_sm; /* fused blocks per SM to launch (1..32, capped by occupancy) */

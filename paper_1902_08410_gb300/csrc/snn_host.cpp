@@ -432,7 +432,7 @@ static int sm_count_cached() {
 
 static void default_launch(snn_net *h) {
   h->cfg.path = 0;
-  h->cfg.update_block = 256;
+  h->cfg.update_block = 128;
   h->cfg.deliver_warps = 4;
   h->cfg.fused_block = 128;
   h->cfg.fused_items_per_sm = 8;
@@ -1328,8 +1328,9 @@ extern "C" int snn_set_launch(snn_handle h, const snn_launch *cfg) {
   if (!h || !cfg) return fail(SNN_ERR_ARG, "null argument");
   const snn_launch &c = *cfg;
   if (c.path != 0 && c.path != 1) return fail(SNN_ERR_ARG, "path must be 0 or 1");
-  if (c.update_block != 128 && c.update_block != 256 && c.update_block != 512)
-    return fail(SNN_ERR_ARG, "update_block must be 128, 256 or 512");
+  if (c.update_block != 64 && c.update_block != 128 && c.update_block != 256 && c.update_block != 512)
+    return fail(SNN_ERR_ARG, "update_block must be 64, 128, 256 or 512");
+  if (c.update_block == 64 && c.update_groups != 1) return fail(SNN_ERR_ARG, "update_block 64 takes update_groups 1");
   if (c.deliver_warps < 1 || c.deliver_warps > 8) return fail(SNN_ERR_ARG, "deliver_warps must be in 1..8");
   if (c.fused_block < 128 || c.fused_block > 512 || c.fused_block % 32)
     return fail(SNN_ERR_ARG, "fused_block must be a multiple of 32 in 128..512");
@@ -1387,8 +1388,9 @@ extern "C" int snn_autotune(snn_handle h, uint32_t trial_steps) {
 
   // stage 1: update shapes with the current delivery shape, and the fused path
   std::vector<snn_launch> cands;
-  for (int ub : {128, 256})
+  for (int ub : {64, 128, 256})
     for (int ug : {1, 2, 4}) {
+      if (ub == 64 && ug != 1) continue;
       snn_launch c = orig;
       c.path = 0;
       c.update_block = ub;

@@ -870,7 +870,7 @@ cudaError_t launch_update(const NetDev &nd, uint32_t k, int block, int groups, c
   const uint32_t blocks = (nd.N_pad + per_block - 1) / per_block;
 #define SNN_UPD(B, G) \
   if (block == B && groups == G) return launch_ex(k_update<B, G>, dim3(blocks), dim3(B), 0, l2, s, nd, k);
-  SNN_UPD(128, 1) SNN_UPD(128, 2) SNN_UPD(128, 4)
+  SNN_UPD(64, 1) SNN_UPD(128, 1) SNN_UPD(128, 2) SNN_UPD(128, 4)
   SNN_UPD(256, 1) SNN_UPD(256, 2) SNN_UPD(256, 4)
   SNN_UPD(512, 1) SNN_UPD(512, 2)
 #undef SNN_UPD
