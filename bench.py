@@ -63,10 +63,11 @@ def parse_args():
                     help="run the two networks one after the other instead of concurrently")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mode", choices=["grid", "batch", "serve", "grid64", "profile"], default="grid",
+    ap.add_argument("--mode", choices=["grid", "batch", "serve", "grid64", "profile", "table_s1"], default="grid",
                     help="grid: 24x24 SWA+AW (default); batch: 256-network SWA->AW sweep; serve: request "
                          "stream; grid64: 64x64 lambda sweep with f32 vs i16 records")
     ap.add_argument("--grid64-steps", type=int, default=50_000)
+    ap.add_argument("--s1-steps", type=int, default=50_000, help="table_s1 mode: measured steps per state")
     # --mode profile: one network, fixed launch shape (the target of ncu captures)
     ap.add_argument("--grid", type=int, default=24)
     ap.add_argument("--regime", choices=["SWA", "AW"], default="AW")
@@ -649,6 +650,51 @@ def _swa_frequency(rates, bin_s):
     return float(f[band][np.argmax(pxx[band])]) if band.any() else None
 
 
+def run_table_s1_mode(args, dist: Dist):
+    """Table S1's three parameter states (recurrent and external efficacies per
+    population, pure Eq. 1 kernel) on the 24x24 grid at lambda 0.4 and 0.6: mean
+    rates per population against the paper's 3.1 / 2.8 / 8.8 Hz, the dominant
+    slow-oscillation frequency, and the throughput on the same kernels."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(dist.local_rank)
+    import paper_1902_08410_gb300 as snn
+    snn.build()
+    warm = 10_000
+    runs = []
+    for lam in (0.4, 0.6):
+        for state, target_hz in (("SW_3.1Hz", 3.1), ("AW_2.8Hz", 2.8), ("AW_8.8Hz", 8.8)):
+            p = W.table_s1_params(24, 24, lam, state)
+            net = snn.Network(p, 1)
+            net.run(warm)
+            st0 = net.stats()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            net.run(args.s1_steps)
+            e1.record()
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            st1 = net.stats()
+            rates = net.rates()[warm // W.BIN_STEPS:]
+            dur = args.s1_steps * W.DT_MS * 1e-3
+            pop_hz = (rates.sum(axis=(0, 1)).astype(np.float64) / (np.array(W.POP_SIZES) * net.G * dur)).tolist()
+            spikes = st1["spikes"] - st0["spikes"]
+            run = {"state": state, "lambda": lam, "paper_rate_hz": target_hz,
+                   "rate_hz": spikes / (net.N * dur), "exc_rate_hz": (pop_hz[0] * 250 + pop_hz[1] * 750) / 1000,
+                   "pop_rate_hz": pop_hz,
+                   "slow_oscillation_hz": _swa_frequency(rates, W.BIN_STEPS * W.DT_MS * 1e-3),
+                   "events_per_s": spikes * EQUIV_PER_SPIKE / sec, "us_per_step": 1e6 * sec / args.s1_steps}
+            runs.append(run)
+            net.close()
+            if dist.rank == 0:
+                print(json.dumps(run), flush=True)
+    if dist.rank == 0:
+        print(json.dumps({"metric": METRIC, "mode": "table_s1", "unit": UNIT, "runs": len(runs), "data": "synthetic",
+                          "config": {"workload": f"24x24 grid, Table S1 efficacies, pure Eq. 1 kernel, {warm} "
+                                                 f"warm-up steps then {args.s1_steps} measured steps, seed 1"}}),
+              flush=True)
+
+
 def run_grid64_mode(args, dist: Dist):
     import numpy as np
     import torch
@@ -730,10 +776,10 @@ def run_profile_mode(args, dist: Dist):
 
 def main():
     args = parse_args()
-    if args.mode in ("batch", "serve", "grid64", "profile"):
+    if args.mode in ("batch", "serve", "grid64", "profile", "table_s1"):
         dist = Dist("nccl")
         try:
-            {"batch": run_batch_mode, "serve": run_serve_mode, "grid64": run_grid64_mode,
+            {"batch": run_batch_mode, "serve": run_serve_mode, "grid64": run_grid64_mode, "table_s1": run_table_s1_mode,
              "profile": run_profile_mode}[args.mode](args, dist)
         finally:
             dist.close()
