@@ -717,10 +717,25 @@ static int drain_absorb(snn_net *h, int b, uint64_t t0, uint32_t n_rec, cudaStre
   if (n_rec) {
     const size_t old = h->raster.size();
     h->raster.resize(old + n_rec);
+    // entries come grouped by step in increasing order (each step's kernels
+    // append before the next step's run); ids within a step are in warp order
+    bool grouped = true;
+    uint64_t prev_k = 0;
+    size_t seg = old;
     for (uint32_t i = 0; i < n_rec; ++i) {
       const unsigned long long e = h->pinned_entries[i];
       const uint64_t k = (e >> 32) & 0xFFFFu;
+      if (k != prev_k) {
+        grouped &= k > prev_k;
+        if (grouped) std::sort(h->raster.begin() + (ptrdiff_t)seg, h->raster.begin() + (ptrdiff_t)(old + i));
+        seg = old + i;
+        prev_k = k;
+      }
       h->raster[old + i] = ((t0 + k) << 32) | (e & 0xFFFFFFFFull);
+    }
+    if (grouped) {
+      std::sort(h->raster.begin() + (ptrdiff_t)seg, h->raster.end());
+      if (h->raster_sorted == old) h->raster_sorted = h->raster.size();   // in order: nothing left to sort
     }
   }
   // rates of the window, bins from t0 / bin_steps
