@@ -603,14 +603,17 @@ def run_serve_mode(args, dist: Dist):
         r["steps"] = max(1, int(round(r["steps"] * args.duration_scale)))
     rate = args.rate
     if rate <= 0:
-        # capacity: neuron-steps per second of the batched path on the first requests
-        sample = reqs[:min(64, len(reqs))]
+        # capacity: neuron-steps per second of the batched path on the first
+        # requests, timed after their initial transient (the first steps fire a
+        # synchronous volley that would make the capacity look far lower)
+        sample = reqs[:min(128, len(reqs))]
         nets = [snn.Network(r["params"], r["seed"]) for r in sample]
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
         snn.run_batch(nets, [1000] * len(nets))
         torch.cuda.synchronize()
-        rate_ns = sum(n.N for n in nets) * 1000 / (time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        snn.run_batch(nets, [2000] * len(nets))
+        torch.cuda.synchronize()
+        rate_ns = sum(n.N for n in nets) * 2000 / (time.perf_counter() - t0)
         for n in nets:
             n.close()
         work = np.mean([W.n_neurons(r["params"]) * r["steps"] for r in reqs])
