@@ -13,6 +13,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -717,25 +718,10 @@ static int drain_absorb(snn_net *h, int b, uint64_t t0, uint32_t n_rec, cudaStre
   if (n_rec) {
     const size_t old = h->raster.size();
     h->raster.resize(old + n_rec);
-    // entries come grouped by step in increasing order (each step's kernels
-    // append before the next step's run); ids within a step are in warp order
-    bool grouped = true;
-    uint64_t prev_k = 0;
-    size_t seg = old;
     for (uint32_t i = 0; i < n_rec; ++i) {
       const unsigned long long e = h->pinned_entries[i];
       const uint64_t k = (e >> 32) & 0xFFFFu;
-      if (k != prev_k) {
-        grouped &= k > prev_k;
-        if (grouped) std::sort(h->raster.begin() + (ptrdiff_t)seg, h->raster.begin() + (ptrdiff_t)(old + i));
-        seg = old + i;
-        prev_k = k;
-      }
       h->raster[old + i] = ((t0 + k) << 32) | (e & 0xFFFFFFFFull);
-    }
-    if (grouped) {
-      std::sort(h->raster.begin() + (ptrdiff_t)seg, h->raster.end());
-      if (h->raster_sorted == old) h->raster_sorted = h->raster.size();   // in order: nothing left to sort
     }
   }
   // rates of the window, bins from t0 / bin_steps
@@ -1141,12 +1127,53 @@ extern "C" int snn_run_concurrent(const snn_handle *hs, const uint64_t *steps, i
 // ---------------------------------------------------------------------------
 // reads
 // ---------------------------------------------------------------------------
+// Order raster[from, end) by (step, id).  Entries arrive grouped by step in
+// increasing order (each step's kernels append before the next step's run),
+// with the ids of a step in warp order, so each step's run is sorted on its
+// own, in parallel over ranges of steps; anything else falls back to one sort.
+static void order_raster(std::vector<unsigned long long> &r, size_t from) {
+  const size_t n = r.size() - from;
+  if (n == 0) return;
+  bool grouped = true;
+  for (size_t i = from + 1; i < r.size() && grouped; ++i) grouped = (r[i] >> 32) >= (r[i - 1] >> 32);
+  if (!grouped) {
+    std::sort(r.begin() + (ptrdiff_t)from, r.end());
+    return;
+  }
+  auto sort_runs = [&r](size_t a, size_t b) {   // [a, b) starts and ends on step boundaries
+    size_t s = a;
+    while (s < b) {
+      size_t e = s + 1;
+      while (e < b && (r[e] >> 32) == (r[s] >> 32)) ++e;
+      std::sort(r.begin() + (ptrdiff_t)s, r.begin() + (ptrdiff_t)e);
+      s = e;
+    }
+  };
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const size_t parts = std::min<size_t>(std::min<size_t>(hw, 16), std::max<size_t>(1, n / (1u << 16)));
+  if (parts <= 1) {
+    sort_runs(from, r.size());
+    return;
+  }
+  std::vector<size_t> cut(parts + 1, r.size());
+  cut[0] = from;
+  for (size_t p = 1; p < parts; ++p) {
+    size_t c = std::max(cut[p - 1], from + n * p / parts);
+    while (c < r.size() && c > from && (r[c] >> 32) == (r[c - 1] >> 32)) ++c;   // move to a step boundary
+    cut[p] = c;
+  }
+  std::vector<std::thread> th;
+  for (size_t p = 0; p < parts; ++p)
+    if (cut[p] < cut[p + 1]) th.emplace_back(sort_runs, cut[p], cut[p + 1]);
+  for (auto &t : th) t.join();
+}
+
 extern "C" int snn_read_spikes(snn_handle h, uint64_t t0, uint64_t t1, uint32_t *step_out, uint32_t *id_out,
                                size_t cap, size_t *n_out) {
   if (!h || !n_out) return fail(SNN_ERR_ARG, "null argument");
   if (h->raster_sorted < h->raster.size()) {
     // records are appended window by window, so only the new tail needs ordering
-    std::sort(h->raster.begin() + (ptrdiff_t)h->raster_sorted, h->raster.end());
+    order_raster(h->raster, h->raster_sorted);
     h->raster_sorted = h->raster.size();
   }
   auto a = t0 > 0xFFFFFFFFull ? h->raster.end()

@@ -252,6 +252,45 @@ def test_launch_shapes_and_autotune_keep_results(snn, oracle_mod):
 
 
 # ---------------------------------------------------------------------------
+# the persisting L2 set-aside is raised while a network with the window lives
+# and the context's previous limit comes back when the last one is freed
+# ---------------------------------------------------------------------------
+def test_l2_set_aside_restored(snn):
+    import ctypes
+    import os
+    cudart = None
+    for cand in (os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "lib64", "libcudart.so"),
+                 "libcudart.so"):
+        try:
+            cudart = ctypes.CDLL(cand)
+            break
+        except OSError:
+            continue
+    if cudart is None:
+        pytest.skip("libcudart.so not found")
+    limit_persisting_l2 = 0x06   # cudaLimitPersistingL2CacheSize
+
+    def limit():
+        v = ctypes.c_size_t(0)
+        assert cudart.cudaDeviceGetLimit(ctypes.byref(v), limit_persisting_l2) == 0
+        return v.value
+
+    before = limit()
+    p = W.base_params(2, 2, 1.0, "AW")
+    a, b = snn.Network(p, 1), snn.Network(p, 2)
+    a.launch = {"l2_persist": 1}
+    b.launch = {"l2_persist": 1}
+    a.run(20)
+    b.run(20)
+    raised = limit()
+    assert raised >= before and raised > 0
+    a.close()
+    assert limit() == raised          # b still holds the window
+    b.close()
+    assert limit() == before
+
+
+# ---------------------------------------------------------------------------
 # bounded waits: a wait that gives up is reported, the context stays usable
 # ---------------------------------------------------------------------------
 def test_wait_limit_zero_reports_timeout(snn):
