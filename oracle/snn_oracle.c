@@ -258,23 +258,37 @@ void orc_synapse(const orc_net *net, uint32_t s, uint32_t j, uint32_t *key, floa
   *key = (d << 24) | tgt;
 }
 
-/* Row of source s: all M synapses, stable-sorted by delay (ties keep j order). */
+/* One drawn synapse before ordering: its record key and its draw index j. */
+typedef struct {
+  uint32_t key;
+  int32_t j;
+} orc_rec;
+
+static int orc_rec_cmp(const void *a, const void *b) {
+  const orc_rec *x = (const orc_rec *)a, *y = (const orc_rec *)b;
+  if (x->key != y->key) return x->key < y->key ? -1 : 1;
+  return (x->j > y->j) - (x->j < y->j);
+}
+
+/* Row of source s: its M synapses ordered by key (delay << 24 | target), i.e.
+ * grouped by delay (Sec. 2.1) and by target within a delay, synapses with the
+ * same delay and target in draw order.  The order is a storage choice: the
+ * delivered sums do not depend on it. */
 void orc_build_row(const orc_net *net, uint32_t s, uint32_t *key_out, float *w_out) {
-  int32_t M = net->M, D = net->D;
-  uint32_t *k = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)M);
+  int32_t M = net->M;
+  orc_rec *r = (orc_rec *)malloc(sizeof(orc_rec) * (size_t)M);
   float *w = (float *)malloc(sizeof(float) * (size_t)M);
-  int32_t *start = (int32_t *)calloc((size_t)D + 1, sizeof(int32_t));
   for (int32_t j = 0; j < M; ++j) {
-    orc_synapse(net, s, (uint32_t)j, &k[j], &w[j]);
-    start[(k[j] >> 24) + 1] += 1;
+    orc_synapse(net, s, (uint32_t)j, &r[j].key, &w[j]);
+    r[j].j = j;
   }
-  for (int32_t d = 0; d < D; ++d) start[d + 1] += start[d];
-  for (int32_t j = 0; j < M; ++j) {
-    int32_t pos = start[k[j] >> 24]++;
-    key_out[pos] = k[j];
-    w_out[pos] = w[j];
+  qsort(r, (size_t)M, sizeof(orc_rec), orc_rec_cmp);
+  for (int32_t p = 0; p < M; ++p) {
+    key_out[p] = r[p].key;
+    w_out[p] = w[r[p].j];
   }
-  free(start); free(w); free(k);
+  free(w);
+  free(r);
 }
 
 static double orc_now(void) {

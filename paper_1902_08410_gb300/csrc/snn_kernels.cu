@@ -522,7 +522,10 @@ __global__ void k_init_state(const __grid_constant__ NetDev nd) {
 
 // ---------------------------------------------------------------------------
 // Kernel: synapse rows (Eq. 1 module choice, uniform target within the module,
-// uniform delay, Gaussian efficacy), each row stable-sorted by delay.
+// uniform delay, Gaussian efficacy), each row ordered by key (delay << 24 |
+// target), records with equal keys in draw order: grouped by delay and sorted
+// by target within a delay, so that the lanes of one delivery instruction
+// often update the same 32-byte sector of the ring.
 // Grid (G, 5): block (m, y) builds rows of module m, local indices
 // [250 y, 250 y + 250).  One warp per row at a time.
 // ---------------------------------------------------------------------------
@@ -536,11 +539,12 @@ __global__ void __launch_bounds__(kBuildWarpsMax * 32) k_build_rows(NetDev nd, B
   const uint32_t cdf_words = cdf_in_smem ? ((Gm1 + 3u) & ~3u) : 0u;
   uint8_t *warp_base = reinterpret_cast<uint8_t *>(s_cdf + cdf_words);
   const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
-  const uint32_t per_warp = nd.M_pad * 10u + 256u * 4u;   // keys, weights, perm (u16), counts
+  const uint32_t per_warp = nd.M_pad * 12u + 256u * 4u;   // keys, weights, counts, two perms (u16)
   uint32_t *w_key = reinterpret_cast<uint32_t *>(warp_base + (size_t)warp * per_warp);
   float *w_w = reinterpret_cast<float *>(w_key + nd.M_pad);
   uint32_t *w_cnt = reinterpret_cast<uint32_t *>(w_w + nd.M_pad);     // 256 counters
-  uint16_t *w_perm = reinterpret_cast<uint16_t *>(w_cnt + 256);
+  uint16_t *w_perm_a = reinterpret_cast<uint16_t *>(w_cnt + 256);
+  uint16_t *w_perm_b = w_perm_a + nd.M_pad;
 
   const uint32_t m = blockIdx.x;
   for (uint32_t i = threadIdx.x; i < (uint32_t)kZTab; i += blockDim.x) s_z[i] = bd.ztab[i];
@@ -558,8 +562,6 @@ __global__ void __launch_bounds__(kBuildWarpsMax * 32) k_build_rows(NetDev nd, B
   for (uint32_t l = blockIdx.y * 250u + warp; l < blockIdx.y * 250u + 250u; l += n_warps) {
     const uint32_t s = m * (uint32_t)kK + l;
     const int sp = pop_of_local(l);
-    for (uint32_t i = lane; i < 256u; i += 32u) w_cnt[i] = 0u;
-    __syncwarp();
     // 1. draw the M synapses of row s
     for (uint32_t j = lane; j < M; j += 32u) {
       const uint4 r = philox4x32_10(s, j, 0u, 0u, nd.key0, nd.key1);
@@ -586,17 +588,28 @@ __global__ void __launch_bounds__(kBuildWarpsMax * 32) k_build_rows(NetDev nd, B
       if (J < 0.0f && w > 0.0f) w = 0.0f;
       w_key[j] = (d << 24) | tgt;
       w_w[j] = w;
-      atomicAdd(&w_cnt[d], 1u);
     }
     __syncwarp();
-    // 2. exclusive scan of the delay counts (256 entries, 8 per lane)
-    {
+    // 2. stable LSD radix sort of the draws by key, one byte per pass: after
+    //    pass b the order is by the key's low b + 1 bytes, equal keys in draw
+    //    order; passes whose byte is the same for every draw leave it as is
+    uint16_t *perm_in = w_perm_a, *perm_out = w_perm_b;
+    for (uint32_t i = lane; i < M; i += 32u) perm_in[i] = (uint16_t)i;
+    for (uint32_t sh = 0; sh < 32u; sh += 8u) {
+      for (uint32_t i = lane; i < 256u; i += 32u) w_cnt[i] = 0u;
+      __syncwarp();
+      for (uint32_t i = lane; i < M; i += 32u) atomicAdd(&w_cnt[(w_key[i] >> sh) & 0xFFu], 1u);
+      __syncwarp();
+      // exclusive scan of the 256 counts (8 per lane); skip a pass with one bucket
       uint32_t v[8], sum = 0;
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         v[q] = w_cnt[lane * 8 + q];
         sum += v[q];
       }
+      const bool one_bucket = __any_sync(0xFFFFFFFFu, v[0] == M || v[1] == M || v[2] == M || v[3] == M ||
+                                                          v[4] == M || v[5] == M || v[6] == M || v[7] == M);
+      if (one_bucket) continue;
       uint32_t incl = sum;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -610,24 +623,25 @@ __global__ void __launch_bounds__(kBuildWarpsMax * 32) k_build_rows(NetDev nd, B
         w_cnt[lane * 8 + q] = acc;
         acc += v[q];
       }
-    }
-    __syncwarp();
-    // 3. stable placement by delay, draws visited in index order
-    for (uint32_t j0 = 0; j0 < M; j0 += 32u) {
-      const uint32_t j = j0 + lane;
-      const bool valid = j < M;
-      const uint32_t d = valid ? (w_key[j] >> 24) : (0x100u + lane);
-      const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
-      const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-      uint32_t pos = 0;
-      if (valid) {
-        pos = w_cnt[d] + rank;
-        w_perm[pos] = (uint16_t)j;
+      __syncwarp();
+      // stable placement, draws visited in the current order
+      for (uint32_t i0 = 0; i0 < M; i0 += 32u) {
+        const uint32_t i = i0 + lane;
+        const bool valid = i < M;
+        const uint32_t e = valid ? perm_in[i] : 0u;
+        const uint32_t dg = valid ? ((w_key[e] >> sh) & 0xFFu) : (0x100u + lane);
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dg);
+        const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+        if (valid) perm_out[w_cnt[dg] + rank] = (uint16_t)e;
+        __syncwarp();
+        if (valid && (__ffs(peers) - 1) == (int)lane) w_cnt[dg] += __popc(peers);
+        __syncwarp();
       }
-      __syncwarp();
-      if (valid && (__ffs(peers) - 1) == (int)lane) w_cnt[d] += __popc(peers);
-      __syncwarp();
+      uint16_t *tmp = perm_in;
+      perm_in = perm_out;
+      perm_out = tmp;
     }
+    const uint16_t *w_perm = perm_in;
     // 4. write the row: keys then weights, padding records zero
     uint8_t *row = nd.rows + (size_t)s * nd.row_bytes;
     uint32_t *okey = reinterpret_cast<uint32_t *>(row);
@@ -829,7 +843,7 @@ cudaError_t launch_init_state(const NetDev &nd, cudaStream_t s) {
 cudaError_t launch_build_rows(const NetDev &h_nd, const BuildDev &bd, cudaStream_t s) {
   const uint32_t Gm1 = h_nd.G - 1u;
   const uint32_t cdf_in_smem = (Gm1 <= 12288u) ? 1u : 0u;
-  const size_t per_warp = (size_t)h_nd.M_pad * 10u + 256u * 4u;
+  const size_t per_warp = (size_t)h_nd.M_pad * 12u + 256u * 4u;
   const size_t fixed = (size_t)kZTab * 4u + (cdf_in_smem ? (((size_t)Gm1 + 3u) & ~(size_t)3u) * 4u : 0u);
   const size_t budget = 200u * 1024u;
   if (fixed + per_warp > budget) return cudaErrorInvalidValue;

@@ -347,7 +347,9 @@ def test_delay_target_weight_laws(oracle_mod):
         assert np.all(np.sign(w[w != 0]) == np.sign(J))
 
 
-def test_rows_are_stable_sorted_by_delay(oracle_mod):
+def test_rows_are_stable_sorted_by_delay_then_target(oracle_mod):
+    """Rows hold the individually drawn synapses ordered by delay, then target,
+    then draw index (NumPy's lexicographic sort of the drawn records)."""
     p = W.base_params(2, 2, 0.4)
     net = oracle_mod.OracleNet(p, 9)
     for s in (0, 777, 1249, 2600, 4999):
@@ -355,10 +357,11 @@ def test_rows_are_stable_sorted_by_delay(oracle_mod):
         raw = [net.synapse(s, j) for j in range(net.M)]
         rk = np.array([r[0] for r in raw], np.uint32)
         rw = np.array([r[1] for r in raw], np.float32)
-        order = np.argsort(rk >> 24, kind="stable")
+        order = np.lexsort((np.arange(len(rk)), rk & 0xFFFFFF, rk >> 24))
         assert np.array_equal(keys, rk[order])
         assert np.array_equal(w, rw[order])
         assert len(keys) == 1125
+        assert np.all(np.diff((keys >> 24).astype(np.int64)) >= 0)
 
 
 def test_pure_kernel_local_share(oracle_mod):
