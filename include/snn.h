@@ -193,6 +193,16 @@ int snn_set_launch(snn_handle h, const snn_launch *cfg);
  * restored afterwards, so results are unchanged. */
 int snn_autotune(snn_handle h, uint32_t trial_steps);
 
+/* The same for a batch advanced by snn_run_batch: fused-kernel shapes (block
+ * size, blocks per SM, delivery chunk) are timed on the whole batch for
+ * `trial_steps` steps each, from snapshots of every network (state, counters
+ * and records restored afterwards, so results are unchanged); the fastest
+ * shape replaces the first network's current shape only if at least 3%
+ * faster, and is set on every network with launch path 1.  The networks must
+ * share one device; the call is ordered on the first network's stream.
+ * Allocates a temporary copy of each network's neuron state and ring. */
+int snn_autotune_batch(const snn_handle *hs, int32_t n, uint32_t trial_steps);
+
 /* Measure the two-kernel path on the next `steps` (1..window) steps, then
  * advance the network by them.  The steps run twice from the same state on the
  * network's stream: once captured into one CUDA graph as snn_run runs them

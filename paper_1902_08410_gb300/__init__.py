@@ -235,6 +235,14 @@ def run_concurrent(nets, steps) -> None:
     _check(lib().snn_run_concurrent(hs, st, len(nets)))
 
 
+def autotune_batch(nets, trial_steps: int = 200) -> dict:
+    """Choose the fused-kernel shape for a batch (see snn_autotune_batch); returns it."""
+    nets = list(nets)
+    hs = (ctypes.c_void_p * len(nets))(*[n.handle.value for n in nets])
+    _check(lib().snn_autotune_batch(hs, len(nets), int(trial_steps)))
+    return nets[0].launch
+
+
 def run_batch(nets, steps) -> None:
     """Advance several networks together with one fused kernel per time step."""
     nets = list(nets)

@@ -1360,6 +1360,119 @@ extern "C" int snn_time_kernels(snn_handle h, uint32_t steps, double *ms_out) {
   return SNN_OK;
 }
 
+// ---------------------------------------------------------------------------
+// batch tuner: fused-kernel shapes timed on the whole batch from snapshots of
+// every network, restored after each trial
+// ---------------------------------------------------------------------------
+extern "C" int snn_autotune_batch(const snn_handle *hs, int32_t n, uint32_t trial_steps) {
+  if (!hs || n < 1) return fail(SNN_ERR_ARG, "empty batch");
+  if (n > 65535) return fail(SNN_ERR_LIMIT, "more than 65535 networks in one batch");
+  if (trial_steps == 0) return fail(SNN_ERR_ARG, "trial_steps must be > 0");
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i]) return fail(SNN_ERR_ARG, "null handle in batch");
+    if (hs[i]->broken) return fail(SNN_ERR_STATE, "network is invalid after an earlier failure");
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return fail(SNN_ERR_ARG, "a network appears twice in the batch");
+  }
+  struct Saved {
+    DevBuf snap;
+    uint64_t t, spikes, ext;
+    size_t raster, sorted;
+    std::vector<uint32_t> rates;
+    snn_launch cfg;
+  };
+  std::vector<Saved> sv((size_t)n);
+  cudaStream_t s = hs[0]->stream;
+  for (int i = 0; i < n; ++i)
+    if (hs[i]->stream != s) CU_TRY(cudaStreamSynchronize(hs[i]->stream));
+  struct G {
+    std::vector<Saved> *v;
+    cudaStream_t s;
+    ~G() {
+      cudaStreamSynchronize(s);
+      for (auto &x : *v) x.snap.release();
+    }
+  } guard{&sv, s};
+  for (int i = 0; i < n; ++i) {
+    snn_net *h = hs[i];
+    int rc = dev_alloc(sv[i].snap, h->L.off_rows);   // V, c, ref, ring
+    if (rc) return rc;
+    CU_TRY(cudaMemcpyAsync(sv[i].snap.p, h->arena.p, h->L.off_rows, cudaMemcpyDeviceToDevice, s));
+    sv[i].t = h->t;
+    sv[i].spikes = h->spikes;
+    sv[i].ext = h->ext_events;
+    sv[i].raster = h->raster.size();
+    sv[i].sorted = h->raster_sorted;
+    sv[i].rates = h->rates;
+    sv[i].cfg = h->cfg;
+  }
+  auto restore = [&]() -> int {
+    for (int i = 0; i < n; ++i) {
+      snn_net *h = hs[i];
+      uint8_t *base = static_cast<uint8_t *>(h->arena.p);
+      CU_TRY(cudaMemcpyAsync(base, sv[i].snap.p, h->L.off_rows, cudaMemcpyDeviceToDevice, s));
+      CU_TRY(cudaMemsetAsync(base + h->L.off_rec[0], 0, h->L.off_entries[0] - h->L.off_rec[0], s));   // both blocks
+      h->t = sv[i].t;
+      h->spikes = sv[i].spikes;
+      h->ext_events = sv[i].ext;
+      h->raster.resize(sv[i].raster);
+      h->raster_sorted = std::min(sv[i].sorted, sv[i].raster);
+      h->rates = sv[i].rates;
+    }
+    return SNN_OK;
+  };
+  cudaEvent_t e0, e1;
+  CU_TRY(cudaEventCreate(&e0));
+  CU_TRY(cudaEventCreate(&e1));
+  std::vector<uint64_t> steps((size_t)n, trial_steps);
+  // one shape on the whole batch: the first pass captures the graphs, the
+  // shape's time is the best of the next `reps` passes
+  auto trial = [&](const snn_launch &c, int reps, float *ms_out) -> int {
+    for (int i = 0; i < n; ++i) hs[i]->cfg = c;
+    *ms_out = 1e30f;
+    for (int rep = 0; rep <= reps; ++rep) {
+      int r = restore();
+      if (r) return r;
+      CU_TRY(cudaEventRecord(e0, s));
+      r = run_fused(hs, steps.data(), n);
+      if (r) return r;
+      CU_TRY(cudaEventRecord(e1, s));
+      CU_TRY(cudaEventSynchronize(e1));
+      float ms = 0;
+      CU_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      if (rep > 0) *ms_out = std::min(*ms_out, ms);
+    }
+    return SNN_OK;
+  };
+  snn_launch orig = hs[0]->cfg;
+  orig.path = 1;
+  float orig_ms = 1e30f, best_ms = 1e30f;
+  snn_launch best = orig;
+  int status = trial(orig, 2, &orig_ms);
+  for (int fb : {128, 256, 512})
+    for (int ips : {2, 4, 8, 16})
+      for (int ch : {64, 128, 192, 256}) {
+        if (status != SNN_OK) break;
+        snn_launch c = orig;
+        c.fused_block = fb;
+        c.fused_items_per_sm = ips;
+        c.deliver_chunk = ch;
+        float ms = 0;
+        status = trial(c, 1, &ms);
+        if (status == SNN_OK && ms < best_ms) {
+          best_ms = ms;
+          best = c;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int rr = restore();
+  CU_TRY(cudaStreamSynchronize(s));
+  const bool replace = status == SNN_OK && best_ms < 0.97f * orig_ms;   // the incumbent unless clearly slower
+  for (int i = 0; i < n; ++i) hs[i]->cfg = (status == SNN_OK) ? (replace ? best : orig) : sv[i].cfg;
+  return status != SNN_OK ? status : rr;
+}
+
 extern "C" int snn_get_launch(snn_handle h, snn_launch *out) {
   if (!h || !out) return fail(SNN_ERR_ARG, "null argument");
   *out = h->cfg;

@@ -184,6 +184,13 @@ def test_batch_matches_oracle(snn, oracle_mod):
     for (p, seed), n, st in zip(params, nets, steps):
         o = _oracle(oracle_mod, p, seed, st + 100)
         _assert_same_run(n, o, st + 100)
+    # the batch tuner restores every network: results continue unchanged
+    cfg = snn.autotune_batch(nets, 30)
+    assert cfg["path"] == 1 and all(n.launch == cfg for n in nets)
+    snn.run_batch(nets, [150] * 4)
+    for (p, seed), n, st in zip(params, nets, steps):
+        o = _oracle(oracle_mod, p, seed, st + 250)
+        _assert_same_run(n, o, st + 250)
 
 
 # ---------------------------------------------------------------------------
