@@ -194,7 +194,9 @@ static void orc_build_pop(orc_net *net, int p) {
   }
 }
 
-/* Thresholds of the target-module distribution of one source module. */
+/* Thresholds of the target-module distribution of one source module: the
+ * exponential decay with distance of Eq. 1 (Sec. 2.2), either as the pure
+ * kernel over all modules or with a fixed local share. */
 static void orc_build_cdf_row(orc_net *net, int32_t ms, uint32_t *T) {
   const orc_params *P = &net->p;
   int32_t G = net->G, gx = P->gx;
@@ -236,7 +238,9 @@ static int32_t orc_pick_module(const uint32_t *T, int32_t G, uint32_t u) {
   return lo;
 }
 
-/* Synapse j of source s: target, delay and weight from one Philox call. */
+/* Synapse j of source s: target module (Eq. 1), target neuron uniform in the
+ * module, delay, and efficacy Gaussian around J (Sec. 2.2), from one Philox
+ * call. */
 void orc_synapse(const orc_net *net, uint32_t s, uint32_t j, uint32_t *key, float *w) {
   const orc_params *P = &net->p;
   uint32_t r[4];
@@ -345,7 +349,8 @@ int orc_neuron_update(const orc_pop *q, float *V, float *c, int32_t *ref, int32_
   return spike;
 }
 
-/* Gaussian-table index (12 bits) of external event e of neuron n at step t;
+/* Gaussian-table index (12 bits) of external event e of neuron n at step t
+ * (external Poisson drive with Gaussian efficacies, Sec. 2.1 and Table S1);
  * `w` is the neuron's 32-bit word of the step's shared draw. */
 static uint32_t orc_ext_index(const orc_net *net, uint32_t w, uint32_t n, uint32_t t, int32_t e) {
   if (e == 0) return w & 0xFFFu;
@@ -407,6 +412,8 @@ orc_net *orc_create(const orc_params *P, uint64_t seed) {
   return net;
 }
 
+/* Record a spike: raster entry and its (5 ms bin, module, population) count
+ * (Sec. 2.3). */
 static void orc_push_spike(orc_net *net, uint32_t t, uint32_t n) {
   if (net->rs_len == net->rs_cap) {
     net->rs_cap = net->rs_cap ? 2 * net->rs_cap : 4096;
@@ -427,6 +434,9 @@ static void orc_push_spike(orc_net *net, uint32_t t, uint32_t n) {
   net->rates[bin * per_bin + (n / ORC_K) * 3 + (size_t)orc_pop_of((int32_t)(n % ORC_K))] += 1;
 }
 
+/* Advance `steps` time steps: every neuron in index order (Eq. 2 with its
+ * input and external drive), then every spike of the step delivered through
+ * its row into the delay ring, sources in ascending order (Sec. 2.1.1). */
 int orc_run(orc_net *net, uint32_t steps) {
   int32_t N = net->N, M = net->M, D = net->D;
   uint32_t *spk = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)N);
