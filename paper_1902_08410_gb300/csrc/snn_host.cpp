@@ -177,6 +177,10 @@ float sign_kept(float w, float mean) {
 
 // Thresholds T[0..G-2] of the target-module distribution of every source
 // module (Eq. 1), built from one table of kernel values per displacement.
+// Eq. 1 thresholds T[src][m] = floor(2^32 * sum_{m' <= m} P(m' | src)) for
+// every source module, in FP64 with the sums taken in module index order.
+// Rows are independent and computed in parallel over host threads; the
+// arithmetic of every row is the same sequence as a serial loop.
 void module_thresholds(const snn_params &p, std::vector<uint32_t> &out) {
   const int gx = p.gx, gy = p.gy, G = gx * gy;
   out.assign((size_t)G * (size_t)(G - 1), 0u);
@@ -188,32 +192,53 @@ void module_thresholds(const snn_params &p, std::vector<uint32_t> &out) {
       const double dx = (double)ax, dy = (double)ay;
       kern[(size_t)ay * gx + ax] = std::exp(-(std::sqrt(dx * dx + dy * dy) / lam));
     }
-  auto kv = [&](int m, int src) {
-    const int ax = std::abs(m % gx - src % gx), ay = std::abs(m / gx - src / gx);
-    return kern[(size_t)ay * gx + ax];
+  auto rows = [&](int src0, int src1) {
+    for (int src = src0; src < src1; ++src) {
+      const int sx = src % gx, sy = src / gx;
+      double total = 0.0;
+      for (int my = 0, m = 0; my < gy; ++my) {
+        const double *krow = kern.data() + (size_t)std::abs(my - sy) * gx;
+        for (int mx = 0; mx < gx; ++mx, ++m) {
+          if (pl >= 0.0 && m == src) continue;
+          total = total + krow[std::abs(mx - sx)];
+        }
+      }
+      double acc = 0.0;
+      uint32_t *T = out.data() + (size_t)src * (size_t)(G - 1);
+      for (int my = 0, m = 0; my < gy; ++my) {
+        const double *krow = kern.data() + (size_t)std::abs(my - sy) * gx;
+        for (int mx = 0; mx < gx && m + 1 < G; ++mx, ++m) {
+          const double k = krow[std::abs(mx - sx)];
+          double pm;
+          if (pl >= 0.0) pm = (m == src) ? pl : ((1.0 - pl) * k) / total;
+          else pm = k / total;
+          acc = acc + pm;
+          const double f = std::floor(acc * 4294967296.0);
+          T[m] = f >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)f;
+        }
+      }
+    }
   };
-  for (int src = 0; src < G; ++src) {
-    double total = 0.0;
-    for (int m = 0; m < G; ++m) {
-      if (pl >= 0.0 && m == src) continue;
-      total = total + kv(m, src);
-    }
-    double acc = 0.0;
-    uint32_t *T = out.data() + (size_t)src * (size_t)(G - 1);
-    for (int m = 0; m + 1 < G; ++m) {
-      double pm;
-      if (pl >= 0.0) pm = (m == src) ? pl : ((1.0 - pl) * kv(m, src)) / total;
-      else pm = kv(m, src) / total;
-      acc = acc + pm;
-      const double f = std::floor(acc * 4294967296.0);
-      T[m] = f >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)f;
-    }
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int parts = (int)std::min<long long>(std::min<unsigned>(hw, 16u), std::max<long long>(1, (long long)G * G / (1 << 16)));
+  if (parts <= 1) {
+    rows(0, G);
+    return;
   }
+  std::vector<std::thread> th;
+  for (int q = 0; q < parts; ++q) th.emplace_back(rows, (int)((long long)G * q / parts), (int)((long long)G * (q + 1) / parts));
+  for (auto &t : th) t.join();
 }
 
+// The table depends on nothing but its size: computed once per process
+// (~250k erfc evaluations), then copied.
 void gaussian_table(std::vector<float> &ztab) {
-  ztab.resize(kZTab);
-  for (int i = 0; i < kZTab; ++i) ztab[i] = (float)inverse_normal_cdf(((double)i + 0.5) / (double)kZTab);
+  static const std::vector<float> table = [] {
+    std::vector<float> z(kZTab);
+    for (int i = 0; i < kZTab; ++i) z[i] = (float)inverse_normal_cdf(((double)i + 0.5) / (double)kZTab);
+    return z;
+  }();
+  ztab = table;
 }
 
 void build_inputs(const snn_params &p, BuildDev &bd) {
