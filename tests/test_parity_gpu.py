@@ -77,6 +77,26 @@ def test_rows_bit_exact(snn, oracle_mod, case):
     g.close()
 
 
+@pytest.mark.parametrize("out_degree", [7, 2048])
+def test_unusual_out_degree_rows_and_run(snn, oracle_mod, out_degree):
+    """Smallest padded row (7 records, M_pad 8) and the largest out-degree
+    (2048): construction layout, sort and delivery at the edges."""
+    p = W.base_params(2, 2, 0.6, "AW", record_format=W.REC_I16)
+    p["out_degree"] = out_degree
+    g = snn.Network(p, 23)
+    o = oracle_mod.OracleNet(p, 23)
+    for s in (0, 250, 1249, 2500, g.N - 1):
+        gk, gw = g.row(s)
+        ok, ow = o.row(s)
+        assert np.array_equal(gk, ok), s
+        q = np.clip(np.rint(ow * np.float32(1024.0)), -32768, 32767).astype(np.float32) / np.float32(1024.0)
+        assert np.array_equal(gw, q), s
+    g.run(300)
+    o.run(300)
+    _assert_same_run(g, o, 300)
+    g.close()
+
+
 def test_rows_bit_exact_full_size_sample(snn, oracle_mod):
     """24x24 grid (720k neurons, 0.81G synapses): sampled rows."""
     p = W.base_params(24, 24, 1.0)
