@@ -23,7 +23,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "--expt-relaxed-constexpr",
               "-Xcompiler", "-fPIC,-ffp-contract=off,-O2,-fno-fast-math", f"-I{INCLUDE}"]
 SOURCES = ["snn_kernels.cu", "snn_host.cpp", "snn_noalloc.cu"]
-HEADERS = ["snn_internal.h"]
+HEADERS = ["snn_internal.h", "snn_raster.h"]
 
 
 def _nvcc() -> str:
