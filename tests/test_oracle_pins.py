@@ -488,3 +488,36 @@ def test_shot_noise_campbell(oracle_mod):
         v = V[sl].astype(np.float64)
         assert abs(v.mean() - m) < 4 * math.sqrt(var / v.size), (v.mean(), m)
         assert abs(v.var() / var - 1) < 4 * math.sqrt(2.0 / v.size) + 0.02, (v.var(), var)
+
+
+def test_external_drive_compound_poisson_cumulants(oracle_mod):
+    """At a high external rate (lam = 3 events per step) the per-step external
+    input is a compound Poisson sum of independent amplitudes drawn from the
+    Gaussian quantile table (Sec. 2.1, Table S1): its cumulants are
+    kappa_n = lam E[a^n], n = 1, 2, 3.  A wrong count law moves kappa_1, an
+    amplitude index shared by two events of one step moves kappa_2 and kappa_3."""
+    p = W.base_params(1, 1, 1.0, "AW")
+    p["nu_ext"] = [75.0, 75.0, 75.0]          # 400 trains x 75 Hz x 0.1 ms = 3
+    p["V_th"] = [1.0e6, 1.0e6, 1.0e6]
+    p["g_c"] = [0.0, 0.0, 0.0]
+    net = oracle_mod.OracleNet(p, 5)
+    T = 2000
+    net.enable_trace(0, T)
+    net.run(T)
+    _, ext = net.trace()
+    assert net.counters()["spikes"] == 0
+    lam = 3.0
+    z = scipy.special.ndtri((np.arange(4096) + 0.5) / 4096.0)
+    for sl, jext in ((slice(0, 1000), 0.858), (slice(1000, 1250), 1.120)):
+        a = jext * (1.0 + 0.25 * z)
+        k = [lam * (a ** n).mean() for n in range(1, 7)]
+        x = ext[:, sl].astype(np.float64).ravel() / 65536.0
+        n = x.size
+        d = x - x.mean()
+        m2, m3 = (d ** 2).mean(), (d ** 3).mean()
+        se1 = math.sqrt(k[1] / n)
+        se2 = math.sqrt((k[3] + 2 * k[1] ** 2) / n)
+        se3 = math.sqrt((k[5] + 9 * k[1] * k[3] + 9 * k[2] ** 2 + 6 * k[1] ** 3) / n)
+        assert abs(x.mean() - k[0]) < 5 * se1, (x.mean(), k[0])
+        assert abs(m2 - k[1]) < 5 * se2, (m2, k[1])
+        assert abs(m3 - k[2]) < 5 * se3, (m3, k[2])
