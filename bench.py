@@ -653,28 +653,23 @@ def run_serve_mode(args, dist: Dist):
 # ---------------------------------------------------------------------------
 # 64x64 grid: lambda sweep, SWA and AW, f32 vs packed i16 records
 # ---------------------------------------------------------------------------
-def _swa_frequency(rates, bin_s):
-    """Dominant frequency (Hz) of the whole-network rate in 0.2..10 Hz (Welch PSD, Sec. 2.3)."""
-    import numpy as np
-    from scipy.signal import welch
-    x = rates.sum(axis=(1, 2)).astype(np.float64)
-    x = x[len(x) // 10:]                      # drop the initial transient
-    x = x - x.mean()
-    f, pxx = welch(x, fs=1.0 / bin_s, nperseg=min(len(x), 512))
-    band = (f >= 0.2) & (f <= 10.0)
-    return float(f[band][np.argmax(pxx[band])]) if band.any() else None
+IMD_MM = 0.4    # inter-module distance in mm (Sec. 3.3.2)
 
 
 def run_table_s1_mode(args, dist: Dist):
     """Table S1's three parameter states (recurrent and external efficacies per
     population, pure Eq. 1 kernel) on the 24x24 grid at lambda 0.4 and 0.6: mean
     rates per population against the paper's 3.1 / 2.8 / 8.8 Hz, the dominant
-    slow-oscillation frequency, and the throughput on the same kernels."""
+    slow-oscillation frequency, the slow-wave speed (Eq. 4, mm/s at 0.4 mm per
+    module; Fig. 7A: faster at larger lambda), and the throughput on the same
+    kernels."""
     import numpy as np
     import torch
     torch.cuda.set_device(dist.local_rank)
     import paper_1902_08410_gb300 as snn
+    from paper_1902_08410_gb300 import analysis
     snn.build()
+    bin_s = W.BIN_STEPS * W.DT_MS * 1e-3
     warm = 10_000
     runs = []
     for lam in (0.4, 0.6):
@@ -697,7 +692,8 @@ def run_table_s1_mode(args, dist: Dist):
             run = {"state": state, "lambda": lam, "paper_rate_hz": target_hz,
                    "rate_hz": spikes / (net.N * dur), "exc_rate_hz": (pop_hz[0] * 250 + pop_hz[1] * 750) / 1000,
                    "pop_rate_hz": pop_hz,
-                   "slow_oscillation_hz": _swa_frequency(rates, W.BIN_STEPS * W.DT_MS * 1e-3),
+                   "slow_oscillation_hz": analysis.dominant_frequency(rates, bin_s),
+                   "slow_waves": analysis.slow_wave_speeds(rates, 24, 24, bin_s, imd=IMD_MM),
                    "events_per_s": spikes * EQUIV_PER_SPIKE / sec, "us_per_step": 1e6 * sec / args.s1_steps}
             runs.append(run)
             net.close()
@@ -715,6 +711,7 @@ def run_grid64_mode(args, dist: Dist):
     import torch
     torch.cuda.set_device(dist.local_rank)
     import paper_1902_08410_gb300 as snn
+    from paper_1902_08410_gb300 import analysis
     snn.build()
     runs = []
     for lam in [float(x) for x in args.grid64_lambdas.split(",")]:
@@ -746,7 +743,7 @@ def run_grid64_mode(args, dist: Dist):
                     "format": "f32" if fmt == W.REC_F32 else "i16", "events_per_s": spikes * EQUIV_PER_SPIKE / sec,
                     "sim_seconds_per_wall_second": sim_s / sec, "us_per_step": 1e6 * sec / args.grid64_steps,
                     "rate_hz": spikes / (net.N * sim_s), "pop_rate_hz": pop_hz,
-                    "swa_frequency_hz": _swa_frequency(rates, W.BIN_STEPS * W.DT_MS * 1e-3),
+                    "swa_frequency_hz": analysis.dominant_frequency(rates, W.BIN_STEPS * W.DT_MS * 1e-3),
                     "bytes_per_recurrent_synapse": st1["device_bytes"] / st1["n_synapses"],
                     "build_seconds": build_s, "launch": cfg,
                 }

@@ -1,0 +1,177 @@
+"""Activity analysis of recorded networks (host, FP64, off the per-step path).
+
+Sec. 2.3 of the paper: module firing rates are sampled in 5 ms bins; power
+spectra use Welch's method; a module's multi-unit activity (MUA) is its mean
+firing rate, analysed as log(MUA / MUA_down) plus zero-mean white noise of
+variance 0.5; for slow-wave activity the Down-to-Up transition time T(x, y) of
+every module defines the wavefront, whose local speed is Eq. 4,
+V = 1 / |grad T|, averaged over all positions.
+
+Readings where the paper leaves the procedure open:
+  * log of a rate that can be zero: the rates are offset by one spike per bin
+    (1 / (K * bin) Hz) before the logarithm, in numerator and denominator.
+  * MUA_down and the threshold: per module, a two-cluster split (k-means on
+    log rate, started at the 10th and 90th percentiles); MUA_down is the mean
+    rate of the lower cluster and the threshold sits midway between the two
+    cluster centres, in log(MUA / MUA_down) units.  A module whose cluster
+    centres lie less than `min_sep` (1.0, a factor e in rate) apart is not
+    bistable: it has no Up states.
+  * Up and Down states are the threshold crossings of the noisy log-MUA; Down
+    runs shorter than `min_down_bins` (10 ms), then Up runs shorter than
+    `min_up_bins` (20 ms), are merged into the surrounding state (dips inside
+    an Up state first, then isolated flickers of the Down state).
+  * A wave is a collective Down-to-Up transition: transitions of all modules,
+    in time order, split wherever consecutive ones are more than `gap_s`
+    apart; each module keeps its first transition of the wave, and waves that
+    reach fewer than half of the modules are dropped.
+  * grad T by central differences in the interior and one-sided differences
+    at the open boundary (numpy.gradient), in units of the inter-module
+    distance; positions where the gradient vanishes or T is missing are left
+    out of the average.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+K = 1250                 # neurons per module (Sec. 2.1)
+
+
+def module_mua(counts: np.ndarray, bin_s: float) -> np.ndarray:
+    """Mean firing rate (Hz) of each module per bin from the integer counters
+    [bin][module][population]: returns [bin][module]."""
+    c = np.asarray(counts, dtype=np.float64)
+    return c.sum(axis=2) / (K * bin_s)
+
+
+def dominant_frequency(counts: np.ndarray, bin_s: float, f_lo: float = 0.2, f_hi: float = 10.0,
+                       skip_frac: float = 0.1) -> float | None:
+    """Peak of the Welch power spectrum of the whole-network rate in [f_lo, f_hi]
+    Hz, after dropping the first `skip_frac` of the record (initial transient)."""
+    from scipy.signal import welch
+    x = np.asarray(counts, dtype=np.float64).sum(axis=(1, 2))
+    x = x[int(len(x) * skip_frac):]
+    if len(x) < 8:
+        return None
+    x = x - x.mean()
+    f, pxx = welch(x, fs=1.0 / bin_s, nperseg=min(len(x), 512))
+    band = (f >= f_lo) & (f <= f_hi)
+    return float(f[band][np.argmax(pxx[band])]) if band.any() else None
+
+
+def _two_means(y: np.ndarray, iters: int = 50) -> tuple[float, float, np.ndarray]:
+    """Two-cluster split of a 1-D sample: (low centre, high centre, is_high)."""
+    lo, hi = np.percentile(y, 10.0), np.percentile(y, 90.0)
+    if hi <= lo:
+        return float(lo), float(hi), np.zeros(y.shape, bool)
+    is_hi = y > 0.5 * (lo + hi)
+    for _ in range(iters):
+        if is_hi.all() or not is_hi.any():
+            break
+        lo, hi = y[~is_hi].mean(), y[is_hi].mean()
+        nxt = y > 0.5 * (lo + hi)
+        if np.array_equal(nxt, is_hi):
+            break
+        is_hi = nxt
+    return float(lo), float(hi), is_hi
+
+
+def log_mua(mua: np.ndarray, bin_s: float, noise_var: float = 0.5, seed: int | None = 0,
+            min_sep: float = 1.0):
+    """log(MUA / MUA_down) per module with white noise of variance `noise_var`
+    added (None seed or zero variance: no noise).  Returns (log_mua [bin][module],
+    threshold [module], inf where the module is not bistable, mua_down [module])."""
+    mua = np.asarray(mua, dtype=np.float64)
+    eps = 1.0 / (K * bin_s)
+    nb, nm = mua.shape
+    out = np.empty_like(mua)
+    thr = np.empty(nm)
+    down = np.empty(nm)
+    rng = np.random.default_rng(seed) if (seed is not None and noise_var > 0) else None
+    for m in range(nm):
+        y = np.log(mua[:, m] + eps)
+        lo, hi, is_hi = _two_means(y)
+        down[m] = mua[~is_hi, m].mean() if (~is_hi).any() else mua[:, m].mean()
+        out[:, m] = np.log((mua[:, m] + eps) / (down[m] + eps))
+        thr[m] = 0.5 * (hi - lo) if hi - lo >= min_sep else np.inf
+    if rng is not None:
+        out += rng.normal(0.0, np.sqrt(noise_var), size=out.shape)
+    return out, thr, down
+
+
+def up_states(lmua: np.ndarray, thr: np.ndarray, min_up_bins: int = 4, min_down_bins: int = 2) -> np.ndarray:
+    """Boolean Up state per bin and module: log-MUA above the module's
+    threshold; interior Down runs shorter than `min_down_bins`, then interior
+    Up runs shorter than `min_up_bins`, are merged into their neighbours."""
+    up = np.asarray(lmua) > np.asarray(thr)[None, :]
+    up = up.copy()
+    for m in range(up.shape[1]):
+        u = up[:, m]
+        for state, min_len in ((False, min_down_bins), (True, min_up_bins)):
+            edges = np.flatnonzero(np.diff(u.astype(np.int8))) + 1
+            starts = np.concatenate(([0], edges))
+            ends = np.concatenate((edges, [len(u)]))
+            for s, e in zip(starts, ends):
+                if u[s] == state and e - s < min_len and s > 0 and e < len(u):
+                    u[s:e] = not state
+        up[:, m] = u
+    return up
+
+
+def down_to_up_times(up: np.ndarray, bin_s: float) -> list[np.ndarray]:
+    """Per module, the times (s, start of the first Up bin) of its Down-to-Up
+    transitions."""
+    up = np.asarray(up)
+    return [(np.flatnonzero(~up[:-1, m] & up[1:, m]) + 1) * bin_s for m in range(up.shape[1])]
+
+
+def waves(times: list[np.ndarray], gx: int, gy: int, gap_s: float = 0.05,
+          min_frac: float = 0.5) -> list[np.ndarray]:
+    """Collective Down-to-Up transitions: list of T[y][x] (s, NaN where a module
+    took no part), one per wave reaching at least `min_frac` of the modules."""
+    ev_t = np.concatenate([np.asarray(t, np.float64) for t in times]) if times else np.zeros(0)
+    ev_m = np.concatenate([np.full(len(t), m) for m, t in enumerate(times)]) if times else np.zeros(0, int)
+    if ev_t.size == 0:
+        return []
+    order = np.argsort(ev_t, kind="stable")
+    ev_t, ev_m = ev_t[order], ev_m[order]
+    cuts = np.flatnonzero(np.diff(ev_t) > gap_s) + 1
+    out = []
+    for idx in np.split(np.arange(ev_t.size), cuts):
+        T = np.full(gx * gy, np.nan)
+        for i in idx:                         # first transition of each module
+            if np.isnan(T[ev_m[i]]):
+                T[ev_m[i]] = ev_t[i]
+        if np.count_nonzero(~np.isnan(T)) >= min_frac * gx * gy:
+            out.append(T.reshape(gy, gx))
+    return out
+
+
+def wave_speed(T: np.ndarray, imd: float = 1.0) -> float:
+    """Eq. 4: mean over positions of V = 1 / |grad T| for one wavefront T[y][x]
+    (s), in units of `imd` per second (imd = inter-module distance)."""
+    T = np.asarray(T, dtype=np.float64)
+    if T.shape[0] < 2 or T.shape[1] < 2:
+        return float("nan")
+    gy_, gx_ = np.gradient(T)                 # per inter-module distance
+    g = np.hypot(gx_, gy_)
+    ok = np.isfinite(g) & (g > 0)
+    if not ok.any():
+        return float("nan")
+    return float(np.mean(imd / g[ok]))
+
+
+def slow_wave_speeds(counts: np.ndarray, gx: int, gy: int, bin_s: float, imd: float = 1.0,
+                     noise_var: float = 0.5, seed: int | None = 0, skip_s: float = 0.0) -> dict:
+    """Whole analysis of Sec. 2.3 on a recorded network: log-MUA, Up/Down
+    states, wavefronts and their mean speeds (Eq. 4).  `counts` are the
+    network's rate counters [bin][module][population]."""
+    c = np.asarray(counts)[int(round(skip_s / bin_s)):]
+    mua = module_mua(c, bin_s)
+    lm, thr, down = log_mua(mua, bin_s, noise_var, seed)
+    up = up_states(lm, thr)
+    ws = waves(down_to_up_times(up, bin_s), gx, gy)
+    speeds = [wave_speed(T, imd) for T in ws]
+    speeds = [s for s in speeds if np.isfinite(s)]
+    return {"waves": len(speeds), "mean_speed": float(np.mean(speeds)) if speeds else None,
+            "sd_speed": float(np.std(speeds)) if speeds else None, "up_fraction": float(up.mean()),
+            "mua_down_hz": float(np.mean(down))}
