@@ -527,27 +527,58 @@ __global__ void k_init_state(const __grid_constant__ NetDev nd) {
 // by target within a delay, so that the lanes of one delivery instruction
 // often update the same 32-byte sector of the ring.
 // Grid (G, 5): block (m, y) builds rows of module m, local indices
-// [250 y, 250 y + 250).  One warp per row at a time.
+// [250 y, 250 y + 250).  One warp per row at a time.  A warp keeps, per draw,
+// the key and the 12-bit quantile index of its efficacy (the weight is formed
+// again when the row is written), so that up to 16 warps share the SM.
 // ---------------------------------------------------------------------------
-constexpr int kBuildWarpsMax = 8;
+constexpr int kBuildWarpsMax = 16;
 
-__global__ void __launch_bounds__(kBuildWarpsMax * 32) k_build_rows(NetDev nd, BuildDev bd, uint32_t cdf_in_smem) {
+// Shared memory of one building warp: keys (u32), 256 counters (u32), then
+// quantile indices and two permutations (u16), rounded up to 16 bytes.
+__host__ __device__ inline uint32_t build_warp_bytes(uint32_t M_pad) {
+  return (M_pad * 10u + 256u * 4u + 15u) & ~15u;
+}
+
+// Bytes of shared memory before the staged CDF: the quantile table, then the
+// efficacy means and spreads (s_js[0] = J, s_js[1] = sigma, [target][source]).
+constexpr uint32_t kBuildTableBytes = kZTab * 4u + 128u;
+
+// Efficacy of a synapse from a population-sp source with key `key` and
+// quantile index z: J + sigma * z-quantile, clamped so it keeps J's sign.
+__device__ __forceinline__ float synapse_weight(const float *s_js, const float *s_z, int sp, uint32_t key,
+                                                uint32_t z) {
+  const uint32_t tgt = key & 0xFFFFFFu;
+  const int tp = pop_of_local(tgt % (uint32_t)kK);
+  const float J = s_js[tp * kNPop + sp];
+  float w = __fadd_rn(J, __fmul_rn(s_js[kNPop * kNPop + tp * kNPop + sp], s_z[z]));
+  if (J > 0.0f && w < 0.0f) w = 0.0f;
+  if (J < 0.0f && w > 0.0f) w = 0.0f;
+  return w;
+}
+
+__global__ void __launch_bounds__(kBuildWarpsMax * 32) k_build_rows(const __grid_constant__ NetDev nd,
+                                                                  const __grid_constant__ BuildDev bd, uint32_t cdf_in_smem) {
   extern __shared__ __align__(128) uint8_t smem[];
   float *s_z = reinterpret_cast<float *>(smem);                       // kZTab
-  uint32_t *s_cdf = reinterpret_cast<uint32_t *>(s_z + kZTab);        // G-1 (if staged)
+  float *s_js = s_z + kZTab;                                          // J, sigma
+  uint32_t *s_cdf = reinterpret_cast<uint32_t *>(smem + kBuildTableBytes);   // G-1 (if staged)
   const uint32_t Gm1 = nd.G - 1u;
   const uint32_t cdf_words = cdf_in_smem ? ((Gm1 + 3u) & ~3u) : 0u;
   uint8_t *warp_base = reinterpret_cast<uint8_t *>(s_cdf + cdf_words);
   const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
-  const uint32_t per_warp = nd.M_pad * 12u + 256u * 4u;   // keys, weights, counts, two perms (u16)
+  const uint32_t per_warp = build_warp_bytes(nd.M_pad);
   uint32_t *w_key = reinterpret_cast<uint32_t *>(warp_base + (size_t)warp * per_warp);
-  float *w_w = reinterpret_cast<float *>(w_key + nd.M_pad);
-  uint32_t *w_cnt = reinterpret_cast<uint32_t *>(w_w + nd.M_pad);     // 256 counters
-  uint16_t *w_perm_a = reinterpret_cast<uint16_t *>(w_cnt + 256);
+  uint32_t *w_cnt = w_key + nd.M_pad;                                  // 256 counters
+  uint16_t *w_z = reinterpret_cast<uint16_t *>(w_cnt + 256);          // quantile index per draw
+  uint16_t *w_perm_a = w_z + nd.M_pad;
   uint16_t *w_perm_b = w_perm_a + nd.M_pad;
 
   const uint32_t m = blockIdx.x;
   for (uint32_t i = threadIdx.x; i < (uint32_t)kZTab; i += blockDim.x) s_z[i] = bd.ztab[i];
+  if (threadIdx.x < (uint32_t)(kNPop * kNPop)) {
+    s_js[threadIdx.x] = bd.J[threadIdx.x / kNPop][threadIdx.x % kNPop];
+    s_js[kNPop * kNPop + threadIdx.x] = bd.sig[threadIdx.x / kNPop][threadIdx.x % kNPop];
+  }
   const uint32_t *cdf_row = bd.cdf + (size_t)m * Gm1;
   if (cdf_in_smem)
     for (uint32_t i = threadIdx.x; i < Gm1; i += blockDim.x) s_cdf[i] = cdf_row[i];
@@ -581,13 +612,8 @@ __global__ void __launch_bounds__(kBuildWarpsMax * 32) k_build_rows(NetDev nd, B
       const uint32_t lt = __umulhi(r.y, (uint32_t)kK);
       const uint32_t tgt = mt * (uint32_t)kK + lt;
       const uint32_t d = 1u + __umulhi(r.z, nd_del);
-      const int tp = pop_of_local(lt);
-      const float J = bd.J[tp][sp];
-      float w = __fadd_rn(J, __fmul_rn(bd.sig[tp][sp], s_z[r.w >> 20]));
-      if (J > 0.0f && w < 0.0f) w = 0.0f;
-      if (J < 0.0f && w > 0.0f) w = 0.0f;
       w_key[j] = (d << 24) | tgt;
-      w_w[j] = w;
+      w_z[j] = (uint16_t)(r.w >> 20);
     }
     __syncwarp();
     // 2. stable LSD radix sort of the draws by key, one byte per pass: after
@@ -651,14 +677,22 @@ __global__ void __launch_bounds__(kBuildWarpsMax * 32) k_build_rows(NetDev nd, B
       for (uint32_t p = lane; p < Mp; p += 32u) {
         int q = 0;
         if (p < M) {
-          q = __float2int_rn(__fmul_rn(w_w[w_perm[p]], 1024.0f));
+          const uint32_t e = w_perm[p];
+          q = __float2int_rn(__fmul_rn(synapse_weight(s_js, s_z, sp, w_key[e], w_z[e]), 1024.0f));
           q = q > 32767 ? 32767 : (q < -32768 ? -32768 : q);
         }
         ow[p] = (int16_t)q;
       }
     } else {
       float *ow = reinterpret_cast<float *>(row + (size_t)Mp * 4u);
-      for (uint32_t p = lane; p < Mp; p += 32u) ow[p] = p < M ? w_w[w_perm[p]] : 0.0f;
+      for (uint32_t p = lane; p < Mp; p += 32u) {
+        float w = 0.0f;
+        if (p < M) {
+          const uint32_t e = w_perm[p];
+          w = synapse_weight(s_js, s_z, sp, w_key[e], w_z[e]);
+        }
+        ow[p] = w;
+      }
     }
     __syncwarp();
   }
@@ -824,13 +858,27 @@ int device_sm_count() {
 static size_t deliver_smem_bytes(int warps, uint32_t chunk) { return (size_t)warps * 2u * chunk * 8u; }
 static size_t fused_smem_bytes(int block) { return (size_t)block * 16u + (size_t)(block / 32) * 2u * kFusedCap * 8u; }
 
+// Dynamic shared memory of one construction block: the device's opt-in
+// maximum per block (227 KB on sm_103), never above 227 KB.
+static size_t build_smem_budget() {
+  static size_t cached = 0;
+  if (cached) return cached;
+  int dev = 0, optin = 0;
+  size_t b = 200u * 1024u;
+  if (cudaGetDevice(&dev) == cudaSuccess &&
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess && optin > 0)
+    b = std::min<size_t>((size_t)optin, 227u * 1024u);
+  cached = b;
+  return b;
+}
+
 cudaError_t prepare_kernels() {
   cudaError_t e = cudaFuncSetAttribute(k_deliver, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)deliver_smem_bytes(8, kStageCap));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem_bytes(512));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_build_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  return cudaFuncSetAttribute(k_build_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)build_smem_budget());
 }
 
 cudaError_t launch_init_state(const NetDev &nd, cudaStream_t s) {
@@ -843,9 +891,9 @@ cudaError_t launch_init_state(const NetDev &nd, cudaStream_t s) {
 cudaError_t launch_build_rows(const NetDev &h_nd, const BuildDev &bd, cudaStream_t s) {
   const uint32_t Gm1 = h_nd.G - 1u;
   const uint32_t cdf_in_smem = (Gm1 <= 12288u) ? 1u : 0u;
-  const size_t per_warp = (size_t)h_nd.M_pad * 12u + 256u * 4u;
-  const size_t fixed = (size_t)kZTab * 4u + (cdf_in_smem ? (((size_t)Gm1 + 3u) & ~(size_t)3u) * 4u : 0u);
-  const size_t budget = 200u * 1024u;
+  const size_t per_warp = build_warp_bytes(h_nd.M_pad);
+  const size_t fixed = (size_t)kBuildTableBytes + (cdf_in_smem ? (((size_t)Gm1 + 3u) & ~(size_t)3u) * 4u : 0u);
+  const size_t budget = build_smem_budget();
   if (fixed + per_warp > budget) return cudaErrorInvalidValue;
   const int warps = (int)std::min<size_t>(kBuildWarpsMax, (budget - fixed) / per_warp);
   const size_t smem = fixed + per_warp * (size_t)warps;
