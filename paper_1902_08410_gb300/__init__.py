@@ -162,8 +162,8 @@ class Network:
         rc = self._lib.snn_read_spikes(self._h, t0, t1, None, None, 0, ctypes.byref(n))
         if rc not in (SNN_OK, -5):
             _check(rc)
-        st = np.zeros(n.value, np.uint32)
-        ids = np.zeros(n.value, np.uint32)
+        st = np.empty(n.value, np.uint32)
+        ids = np.empty(n.value, np.uint32)
         _check(self._lib.snn_read_spikes(self._h, t0, t1, _ptr(st), _ptr(ids), n.value, ctypes.byref(n)))
         return st, ids
 

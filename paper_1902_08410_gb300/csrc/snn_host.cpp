@@ -1170,11 +1170,7 @@ extern "C" int snn_read_spikes(snn_handle h, uint64_t t0, uint64_t t1, uint32_t 
   *n_out = n;
   if (n > cap) return fail(SNN_ERR_BUFFER, "spike buffer too small");
   if (n && (!step_out || !id_out)) return fail(SNN_ERR_ARG, "null output buffer");
-  size_t i = 0;
-  for (auto it = a; it != b; ++it, ++i) {
-    step_out[i] = (uint32_t)(*it >> 32);
-    id_out[i] = (uint32_t)(*it & 0xFFFFFFFFull);
-  }
+  if (n) split_raster(&*a, n, step_out, id_out);
   return SNN_OK;
 }
 

@@ -5,6 +5,7 @@
 #pragma once
 #include <algorithm>
 #include <cstddef>
+#include <cstdint>
 #include <thread>
 #include <utility>
 #include <vector>
@@ -76,6 +77,26 @@ inline void order_raster(std::vector<unsigned long long> &r, size_t from) {
   for (size_t p = 1; p < parts && ok; ++p)   // ranges in order at their boundaries
     if (cut[p] > from && cut[p] < r.size()) ok &= (r[cut[p]] >> 32) > (r[cut[p] - 1] >> 32);
   if (!ok) std::sort(r.begin() + (ptrdiff_t)from, r.end());
+}
+
+// Split entries a[0, n) into step and id arrays, in parallel over ranges for
+// large reads.
+inline void split_raster(const unsigned long long *a, size_t n, uint32_t *step_out, uint32_t *id_out) {
+  auto work = [=](size_t lo, size_t hi) {
+    for (size_t i = lo; i < hi; ++i) {
+      step_out[i] = (uint32_t)(a[i] >> 32);
+      id_out[i] = (uint32_t)(a[i] & 0xFFFFFFFFull);
+    }
+  };
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const size_t parts = std::min<size_t>(std::min<size_t>(hw, 16), std::max<size_t>(1, n / (1u << 20)));
+  if (parts <= 1) {
+    work(0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (size_t p = 0; p < parts; ++p) th.emplace_back(work, n * p / parts, n * (p + 1) / parts);
+  for (auto &t : th) t.join();
 }
 
 }  // namespace snn

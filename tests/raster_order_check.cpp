@@ -2,7 +2,8 @@
 // rasters built like the library builds them (entries grouped by step in
 // increasing order, the ids of a step shuffled), with and without an already
 // ordered head, and rasters that are not grouped by step (the fallback), must
-// come out exactly as std::sort orders them.  Exit status 0 on success.
+// come out exactly as std::sort orders them; the split into step and id arrays
+// must reproduce every entry.  Exit status 0 on success.
 #include <algorithm>
 #include <cstdint>
 #include <cstdio>
@@ -35,6 +36,19 @@ int main() {
     if (r != ref) {
       ++fails;
       std::printf("trial %d: order differs (%zu entries)\n", trial, r.size());
+    }
+  }
+  // split into step and id arrays: below and above the parallel threshold
+  for (size_t n : {(size_t)0, (size_t)1, (size_t)1000, (size_t)5000003}) {
+    std::vector<unsigned long long> r(n);
+    for (size_t i = 0; i < n; ++i) r[i] = ((unsigned long long)(i / 7) << 32) | (uint32_t)(rng() % (1u << 24));
+    std::vector<uint32_t> st(n + 1, 0xDEADBEEFu), id(n + 1, 0xDEADBEEFu);
+    snn::split_raster(r.data(), n, st.data(), id.data());
+    bool ok = st[n] == 0xDEADBEEFu && id[n] == 0xDEADBEEFu;
+    for (size_t i = 0; i < n && ok; ++i) ok = st[i] == (uint32_t)(r[i] >> 32) && id[i] == (uint32_t)r[i];
+    if (!ok) {
+      ++fails;
+      std::printf("split of %zu entries differs\n", n);
     }
   }
   std::printf("%s\n", fails ? "FAIL" : "ok");
