@@ -16,14 +16,16 @@ Readings where the paper leaves the procedure open:
     cluster centres, in log(MUA / MUA_down) units.  A module whose cluster
     centres lie less than `min_sep` (1.0, a factor e in rate) apart is not
     bistable: it has no Up states.
-  * Up and Down states are the threshold crossings of the noisy log-MUA; Down
-    runs shorter than `min_down_bins` (10 ms), then Up runs shorter than
-    `min_up_bins` (20 ms), are merged into the surrounding state (dips inside
-    an Up state first, then isolated flickers of the Down state).
-  * A wave is a collective Down-to-Up transition: transitions of all modules,
-    in time order, split wherever consecutive ones are more than `gap_s`
-    apart; each module keeps its first transition of the wave, and waves that
-    reach fewer than half of the modules are dropped.
+  * Up and Down states are the threshold crossings of the noisy log-MUA,
+    cleaned in three passes: single-bin Up flickers are dropped, then Down
+    runs shorter than `min_down_bins` (dips inside an Up state) and Up runs
+    shorter than `min_up_bins` (both 20 ms) are merged into the surrounding
+    state.
+  * A wave is a collective Down-to-Up transition: the transitions of all
+    modules, in time order, are cut into waves wherever consecutive ones are
+    more than `gap_s` apart or a module would take part twice (each module
+    transits at most once per wave); waves that reach fewer than half of the
+    modules are dropped.
   * grad T by central differences in the interior and one-sided differences
     at the open boundary (numpy.gradient), in units of the inter-module
     distance; positions where the gradient vanishes or T is missing are left
@@ -98,15 +100,16 @@ def log_mua(mua: np.ndarray, bin_s: float, noise_var: float = 0.5, seed: int | N
     return out, thr, down
 
 
-def up_states(lmua: np.ndarray, thr: np.ndarray, min_up_bins: int = 4, min_down_bins: int = 2) -> np.ndarray:
+def up_states(lmua: np.ndarray, thr: np.ndarray, min_up_bins: int = 4, min_down_bins: int = 4) -> np.ndarray:
     """Boolean Up state per bin and module: log-MUA above the module's
-    threshold; interior Down runs shorter than `min_down_bins`, then interior
-    Up runs shorter than `min_up_bins`, are merged into their neighbours."""
+    threshold; interior single-bin Up runs, then Down runs shorter than
+    `min_down_bins`, then Up runs shorter than `min_up_bins`, are merged into
+    their neighbours."""
     up = np.asarray(lmua) > np.asarray(thr)[None, :]
     up = up.copy()
     for m in range(up.shape[1]):
         u = up[:, m]
-        for state, min_len in ((False, min_down_bins), (True, min_up_bins)):
+        for state, min_len in ((True, 2), (False, min_down_bins), (True, min_up_bins)):
             edges = np.flatnonzero(np.diff(u.astype(np.int8))) + 1
             starts = np.concatenate(([0], edges))
             ends = np.concatenate((edges, [len(u)]))
@@ -134,15 +137,19 @@ def waves(times: list[np.ndarray], gx: int, gy: int, gap_s: float = 0.05,
         return []
     order = np.argsort(ev_t, kind="stable")
     ev_t, ev_m = ev_t[order], ev_m[order]
-    cuts = np.flatnonzero(np.diff(ev_t) > gap_s) + 1
     out = []
-    for idx in np.split(np.arange(ev_t.size), cuts):
-        T = np.full(gx * gy, np.nan)
-        for i in idx:                         # first transition of each module
-            if np.isnan(T[ev_m[i]]):
-                T[ev_m[i]] = ev_t[i]
+    T = np.full(gx * gy, np.nan)
+
+    def close(T):
         if np.count_nonzero(~np.isnan(T)) >= min_frac * gx * gy:
             out.append(T.reshape(gy, gx))
+
+    for i in range(ev_t.size):
+        if i > 0 and (ev_t[i] - ev_t[i - 1] > gap_s or not np.isnan(T[ev_m[i]])):
+            close(T)
+            T = np.full(gx * gy, np.nan)
+        T[ev_m[i]] = ev_t[i]
+    close(T)
     return out
 
 

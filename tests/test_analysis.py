@@ -81,6 +81,21 @@ def test_slow_wave_pipeline_recovers_planar_wave():
     assert out["up_fraction"] == pytest.approx(4 * 0.3 / (5 * 2.0), abs=0.01)
 
 
+def test_back_to_back_waves_are_separated():
+    """Waves every 0.4 s that each take 0.375 s to cross the grid leave no
+    quiet gap between them; each module transits once per wave, so every wave
+    is still found on its own, with its speed."""
+    bin_s, v = 0.005, 40.0
+    counts, onsets = _planar_wave_counts(16, 10, v, 0.4, 0.15, 10, bin_s, 20.0, 0.3, seed=4)
+    mua = A.module_mua(counts, bin_s)
+    lm, thr, _ = A.log_mua(mua, bin_s, noise_var=0.5, seed=2)
+    ws = A.waves(A.down_to_up_times(A.up_states(lm, thr), bin_s), 16, 10)
+    assert len(ws) == 10
+    for T, T0 in zip(ws, onsets):
+        assert np.median(np.abs(T - T0)) <= bin_s + 1e-12
+    assert A.slow_wave_speeds(counts, 16, 10, bin_s)["mean_speed"] == pytest.approx(v, rel=0.05)
+
+
 def test_asynchronous_activity_has_no_collective_waves():
     """Stationary Poisson firing (no Up/Down alternation) yields no wave that
     reaches half the modules."""
