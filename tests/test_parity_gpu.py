@@ -148,6 +148,27 @@ def test_run_small_grids(snn, oracle_mod, grid, regime):
     _assert_same_run(g, o, 501)
 
 
+@pytest.mark.parametrize("n_delay,bin_steps,dt_ms", [(1, 50, 0.1), (254, 7, 0.1), (20, 50, 0.05)])
+def test_delay_range_bins_and_time_step(snn, oracle_mod, n_delay, bin_steps, dt_ms):
+    """Ring depth at both ends (every delay one step: D = 2; delays up to 254
+    steps: D = 255), rate bins that do not divide the windows, and a finer time
+    step (propagators, Poisson rate and refractory steps all change), over runs
+    split across windows, on both record formats."""
+    for fmt in (W.REC_F32, W.REC_I16):
+        p = W.base_params(2, 2, 0.6, "AW", record_format=fmt)
+        p["n_delay"], p["bin_steps"], p["dt_ms"] = n_delay, bin_steps, dt_ms
+        g = snn.Network(p, 29)
+        for n in (3, 400, 97):
+            g.run(n)
+        o = _oracle(oracle_mod, p, 29, 500)
+        ok, _ = o.row(1000)
+        gk, _ = g.row(1000)
+        assert np.array_equal(gk, ok)
+        assert int((ok >> 24).max()) <= n_delay
+        _assert_same_run(g, o, 500)
+        g.close()
+
+
 def test_run_table_s1_pure_kernel(snn, oracle_mod):
     """Table S1 three-population efficacies with the pure Eq. 1 kernel."""
     p = W.table_s1_params(3, 3, 0.6, "AW_8.8Hz")
