@@ -448,6 +448,15 @@ def run_gb300(args, dist: Dist):
                 "step_ms": {names[j]: net_step_ms[j] for j in range(len(nets))},
                 "kernels": {k: {**v, "frac": v["achieved_gbs"] / peak, "share": share[k]} for k, v in kernels.items()}}
 
+    # ---- activity of the simulated networks (host analysis of the binned rates, Sec. 2.3)
+    from paper_1902_08410_gb300 import analysis
+    bin_s = W.BIN_STEPS * W.DT_MS * 1e-3
+    activity = []
+    for n in nets:
+        r = n.rates()
+        activity.append({"slow_oscillation_hz": analysis.dominant_frequency(r, bin_s),
+                         "slow_waves": analysis.slow_wave_speeds(r, 24, 24, bin_s, imd=IMD_MM, skip_s=1.0)})
+
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -505,7 +514,8 @@ def run_gb300(args, dist: Dist):
                        else "concurrently, one CUDA stream each (snn_run_concurrent)"},
             "sim_seconds_per_wall_second": sim_s * len(nets) * dist.world / t_max,
             "per_regime": {names[i]: {"spikes": spikes[i], "rate_hz": spikes[i] / (nets[i].N * sim_s),
-                                      "recurrent_events": spikes[i] * W.OUT_DEGREE, "external_events": ext[i]}
+                                      "recurrent_events": spikes[i] * W.OUT_DEGREE, "external_events": ext[i],
+                                      **activity[i]}
                            for i in range(len(nets))},
             "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clocks,
             "paper_context": "2.3e9-4.1e9 equivalent synaptic events/s on up to 1024 Haswell cores (Abstract)",
@@ -744,6 +754,8 @@ def run_grid64_mode(args, dist: Dist):
                     "sim_seconds_per_wall_second": sim_s / sec, "us_per_step": 1e6 * sec / args.grid64_steps,
                     "rate_hz": spikes / (net.N * sim_s), "pop_rate_hz": pop_hz,
                     "swa_frequency_hz": analysis.dominant_frequency(rates, W.BIN_STEPS * W.DT_MS * 1e-3),
+                    "slow_waves": analysis.slow_wave_speeds(rates, 64, 64, W.BIN_STEPS * W.DT_MS * 1e-3,
+                                                            imd=IMD_MM, skip_s=0.5),
                     "bytes_per_recurrent_synapse": st1["device_bytes"] / st1["n_synapses"],
                     "build_seconds": build_s, "launch": cfg,
                 }

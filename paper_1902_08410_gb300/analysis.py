@@ -60,21 +60,26 @@ def dominant_frequency(counts: np.ndarray, bin_s: float, f_lo: float = 0.2, f_hi
     return float(f[band][np.argmax(pxx[band])]) if band.any() else None
 
 
-def _two_means(y: np.ndarray, iters: int = 50) -> tuple[float, float, np.ndarray]:
-    """Two-cluster split of a 1-D sample: (low centre, high centre, is_high)."""
-    lo, hi = np.percentile(y, 10.0), np.percentile(y, 90.0)
-    if hi <= lo:
-        return float(lo), float(hi), np.zeros(y.shape, bool)
-    is_hi = y > 0.5 * (lo + hi)
+def _two_means(y: np.ndarray, iters: int = 50) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Two-cluster split (k-means, k = 2) of every column of y [sample][column]:
+    (low centres, high centres, is_high)."""
+    lo, hi = np.percentile(np.ascontiguousarray(y.T), [10.0, 90.0], axis=1)
+    flat = hi <= lo
+    is_hi = (y > 0.5 * (lo + hi)) & ~flat
     for _ in range(iters):
-        if is_hi.all() or not is_hi.any():
-            break
-        lo, hi = y[~is_hi].mean(), y[is_hi].mean()
-        nxt = y > 0.5 * (lo + hi)
-        if np.array_equal(nxt, is_hi):
+        n_hi = is_hi.sum(axis=0)
+        n_lo = y.shape[0] - n_hi
+        ok = (n_hi > 0) & (n_lo > 0)
+        s_hi = np.where(is_hi, y, 0.0).sum(axis=0)
+        s_all = y.sum(axis=0)
+        lo = np.where(ok, (s_all - s_hi) / np.maximum(n_lo, 1), lo)
+        hi = np.where(ok, s_hi / np.maximum(n_hi, 1), hi)
+        nxt = (y > 0.5 * (lo + hi)) & ~flat & ok
+        if np.array_equal(nxt, is_hi & ok):
+            is_hi = nxt
             break
         is_hi = nxt
-    return float(lo), float(hi), is_hi
+    return lo, hi, is_hi
 
 
 def log_mua(mua: np.ndarray, bin_s: float, noise_var: float = 0.5, seed: int | None = 0,
@@ -84,17 +89,16 @@ def log_mua(mua: np.ndarray, bin_s: float, noise_var: float = 0.5, seed: int | N
     threshold [module], inf where the module is not bistable, mua_down [module])."""
     mua = np.asarray(mua, dtype=np.float64)
     eps = 1.0 / (K * bin_s)
-    nb, nm = mua.shape
+    nm = mua.shape[1]
     out = np.empty_like(mua)
     thr = np.empty(nm)
     down = np.empty(nm)
     rng = np.random.default_rng(seed) if (seed is not None and noise_var > 0) else None
-    for m in range(nm):
-        y = np.log(mua[:, m] + eps)
-        lo, hi, is_hi = _two_means(y)
-        down[m] = mua[~is_hi, m].mean() if (~is_hi).any() else mua[:, m].mean()
-        out[:, m] = np.log((mua[:, m] + eps) / (down[m] + eps))
-        thr[m] = 0.5 * (hi - lo) if hi - lo >= min_sep else np.inf
+    lo, hi, is_hi = _two_means(np.log(mua + eps))
+    n_lo = (~is_hi).sum(axis=0)
+    down[:] = np.where(n_lo > 0, np.where(is_hi, 0.0, mua).sum(axis=0) / np.maximum(n_lo, 1), mua.mean(axis=0))
+    out[:] = np.log((mua + eps) / (down + eps))
+    thr[:] = np.where(hi - lo >= min_sep, 0.5 * (hi - lo), np.inf)
     if rng is not None:
         out += rng.normal(0.0, np.sqrt(noise_var), size=out.shape)
     return out, thr, down
@@ -107,7 +111,7 @@ def up_states(lmua: np.ndarray, thr: np.ndarray, min_up_bins: int = 4, min_down_
     their neighbours."""
     up = np.asarray(lmua) > np.asarray(thr)[None, :]
     up = up.copy()
-    for m in range(up.shape[1]):
+    for m in np.flatnonzero(up.any(axis=0)):
         u = up[:, m]
         for state, min_len in ((True, 2), (False, min_down_bins), (True, min_up_bins)):
             edges = np.flatnonzero(np.diff(u.astype(np.int8))) + 1
