@@ -175,14 +175,20 @@ def slow_wave_speeds(counts: np.ndarray, gx: int, gy: int, bin_s: float, imd: fl
                      noise_var: float = 0.5, seed: int | None = 0, skip_s: float = 0.0) -> dict:
     """Whole analysis of Sec. 2.3 on a recorded network: log-MUA, Up/Down
     states, wavefronts and their mean speeds (Eq. 4).  `counts` are the
-    network's rate counters [bin][module][population]."""
+    network's rate counters [bin][module][population].  `waves` counts the
+    collective transitions found, `timed_waves` those with a finite speed (a
+    wavefront that reaches every module within one bin has none)."""
     c = np.asarray(counts)[int(round(skip_s / bin_s)):]
     mua = module_mua(c, bin_s)
     lm, thr, down = log_mua(mua, bin_s, noise_var, seed)
     up = up_states(lm, thr)
-    ws = waves(down_to_up_times(up, bin_s), gx, gy)
+    times = down_to_up_times(up, bin_s)
+    ws = waves(times, gx, gy)
     speeds = [wave_speed(T, imd) for T in ws]
     speeds = [s for s in speeds if np.isfinite(s)]
-    return {"waves": len(speeds), "mean_speed": float(np.mean(speeds)) if speeds else None,
-            "sd_speed": float(np.std(speeds)) if speeds else None, "up_fraction": float(up.mean()),
-            "mua_down_hz": float(np.mean(down))}
+    return {"waves": len(ws), "timed_waves": len(speeds),
+            "mean_speed": float(np.mean(speeds)) if speeds else None,
+            "sd_speed": float(np.std(speeds)) if speeds else None,
+            "transitions_per_module_s": float(sum(len(t) for t in times)) / (up.shape[1] * up.shape[0] * bin_s)
+            if up.size else 0.0,
+            "up_fraction": float(up.mean()) if up.size else 0.0, "mua_down_hz": float(np.mean(down))}
