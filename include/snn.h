@@ -233,9 +233,13 @@ int snn_time_kernels(snn_handle h, uint32_t steps, double *ms_out);
  * Scratch (module thresholds, Gaussian table) lives in one static device array
  * of about 4.2 MB that every GPU loading the library holds until exit, so the
  * grid may have at most 1024 modules (SNN_ERR_LIMIT beyond).  The first call
- * on a device looks up that array's address; make it before any stream
- * capture.  All calls share the array: calls whose work overlaps on the GPU
- * race and must be ordered by the caller (for example on one stream).
+ * on a device (the size query included) looks up that array's address, which
+ * loads the library's device code and places the array on the device: make a
+ * size query before reserving the rest of the device's memory.  The call
+ * uploads its tables from host memory it frees on return, so it refuses a
+ * stream that is being captured (SNN_ERR_ARG).  All calls share the array:
+ * calls whose work overlaps on the GPU race and must be ordered by the caller
+ * (for example on one stream).
  * Errors: SNN_ERR_ARG, SNN_ERR_LIMIT, SNN_ERR_BUFFER (rows_bytes too small),
  * SNN_ERR_CUDA. */
 int snn_build_rows_static(const snn_params *p, uint64_t seed, void *rows_out, size_t *rows_bytes,

@@ -2,10 +2,11 @@
 
 TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may use this package; the product path never
-does.  The simulator itself is plain C (``snn_oracle.c``), single-threaded,
-compiled with ``-O2 -ffp-contract=off`` so that each float operation is one
-correctly rounded binary32 operation in source order.  It shares no code with
-the CUDA path.
+does.  The simulator itself is plain C (``snn_oracle.c``), compiled with
+``-O2 -ffp-contract=off`` so that each float operation is one correctly rounded
+binary32 operation in source order; it steps on one thread (the tests may let
+extra threads generate synapse rows, pure functions of seed and source).  It
+shares no code with the CUDA path.
 """
 from __future__ import annotations
 
@@ -33,7 +34,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm", "-lpthread"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -112,6 +113,7 @@ def _load():
     lib.orc_philox4x32_10.argtypes = [vp, u32, u32, vp]
     lib.orc_row_build_seconds.restype = ctypes.c_double
     lib.orc_row_build_seconds.argtypes = [vp]
+    lib.orc_configure_rows.argtypes = [vp, i32, i32]
     lib.orc_inv_phi.restype = ctypes.c_double
     lib.orc_inv_phi.argtypes = [ctypes.c_double]
     _lib = lib
@@ -205,6 +207,11 @@ class OracleNet:
         self._lib.orc_ring(self._h, _ptr(out))
         return out
 
+    def configure_rows(self, threads: int = 1, keep: bool = True) -> None:
+        """Test-harness setting with no effect on results: threads that generate
+        the rows a step needs, and whether generated rows stay cached."""
+        self._lib.orc_configure_rows(self._h, int(threads), 1 if keep else 0)
+
     def row_build_seconds(self) -> float:
         """Wall time the oracle spent generating rows on first use."""
         return self._lib.orc_row_build_seconds(self._h)
@@ -265,3 +272,20 @@ class OracleNet:
         ext = np.zeros((self._trace_steps, self.N), np.int32)
         self._lib.orc_trace(self._h, _ptr(rec), _ptr(ext))
         return rec, ext
+
+
+def simulate(params: dict, seed: int, steps: int, row_threads: int = 1, keep_rows: bool = True) -> dict:
+    """Run one network for `steps` steps from its initial state and return every
+    result the parity tests compare: raster (steps, ids), rate counts, final
+    V, c and refractory counters, and the event counters.  A plain function so
+    that a spawned process pool can run it."""
+    o = OracleNet(params, seed)
+    try:
+        o.configure_rows(row_threads, keep_rows)
+        o.run(steps)
+        ts, ids = o.raster()
+        V, c, ref = o.state()
+        return {"t": o.t, "steps": ts, "ids": ids, "rates": o.rates(), "V": V, "c": c, "ref": ref,
+                "counters": o.counters(), "row_build_seconds": o.row_build_seconds()}
+    finally:
+        o.close()

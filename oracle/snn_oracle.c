@@ -7,6 +7,10 @@
  * code, header or table generator with the CUDA path; both are written from
  * the paper and from the step contract below.
  *
+ * The simulation runs on the calling thread.  The tests may let several
+ * threads generate the synapse rows a step needs (orc_configure_rows): a row
+ * is a pure function of (seed, source), so this changes no result.
+ *
  * Compile with -O2 -ffp-contract=off and no fast-math: every float operation
  * below is one IEEE-754 binary32 operation rounded to nearest, in the order
  * written, with no fused multiply-add.
@@ -41,6 +45,7 @@
  *   ring[(t + d) mod D][target].
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -51,6 +56,7 @@
 #define ORC_KMAX 16
 #define ORC_FMT_F32 0
 #define ORC_FMT_I16 1
+#define ORC_ROW_BATCH 16384   /* spikes whose rows are generated together */
 
 typedef struct {
   int32_t gx, gy;
@@ -89,6 +95,8 @@ typedef struct {
   int32_t *ring;            /* [D][N] */
   uint32_t **row_key;       /* lazily generated rows (pure functions of seed, source) */
   float **row_w;
+  int32_t row_threads;      /* threads that generate a step's missing rows (1 = this thread) */
+  int32_t keep_rows;        /* 1: rows stay cached after use; 0: freed after the step's delivery */
   uint32_t t;
   /* records */
   uint32_t *rs_t, *rs_n;
@@ -301,16 +309,64 @@ static double orc_now(void) {
   return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
 }
 
-static void orc_ensure_row(orc_net *net, uint32_t s) {
-  if (net->row_key[s]) return;
-  double t_in = orc_now();
+static void orc_make_row(orc_net *net, uint32_t s) {
   net->row_key[s] = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)net->M);
   net->row_w[s] = (float *)malloc(sizeof(float) * (size_t)net->M);
   orc_build_row(net, s, net->row_key[s], net->row_w[s]);
+}
+
+/* Rows of a list of sources generated by several threads.  A row is a pure
+ * function of (seed, source) and each thread writes only its own sources'
+ * slots, so the result does not depend on how the list is split. */
+typedef struct {
+  orc_net *net;
+  const uint32_t *src;
+  int32_t n, first, stride;
+} orc_row_job;
+
+static void *orc_row_worker(void *arg) {
+  orc_row_job *job = (orc_row_job *)arg;
+  for (int32_t i = job->first; i < job->n; i += job->stride) orc_make_row(job->net, job->src[i]);
+  return NULL;
+}
+
+static void orc_make_rows(orc_net *net, const uint32_t *src, int32_t n) {
+  double t_in = orc_now();
+  int32_t T = net->row_threads;
+  if (T > 64) T = 64;
+  if (T > n) T = n;
+  if (T <= 1) {
+    for (int32_t i = 0; i < n; ++i) orc_make_row(net, src[i]);
+  } else {
+    pthread_t th[64];
+    orc_row_job jobs[64];
+    int32_t started = 0;
+    for (int32_t k = 0; k < T; ++k) {
+      jobs[k].net = net; jobs[k].src = src; jobs[k].n = n; jobs[k].first = k; jobs[k].stride = T;
+      if (pthread_create(&th[k], NULL, orc_row_worker, &jobs[k]) != 0) break;
+      ++started;
+    }
+    /* whatever could not be handed to a thread is generated here */
+    for (int32_t k = started; k < T; ++k) orc_row_worker(&jobs[k]);
+    for (int32_t k = 0; k < started; ++k) pthread_join(th[k], NULL);
+  }
   net->row_build_seconds += orc_now() - t_in;
 }
 
+static void orc_drop_row(orc_net *net, uint32_t s) {
+  free(net->row_key[s]); free(net->row_w[s]);
+  net->row_key[s] = NULL; net->row_w[s] = NULL;
+}
+
 double orc_row_build_seconds(const orc_net *net) { return net->row_build_seconds; }
+
+/* Test-harness setting, no effect on results: how many threads generate the
+ * rows a step needs, and whether rows stay cached (a 5M-neuron grid needs
+ * ~46 GB to cache every row). */
+void orc_configure_rows(orc_net *net, int32_t threads, int32_t keep) {
+  net->row_threads = threads < 1 ? 1 : threads;
+  net->keep_rows = keep ? 1 : 0;
+}
 
 /* Fixed-point weight (2^-16 mV) delivered by one record. */
 static int32_t orc_wfix(const orc_net *net, float w) {
@@ -402,6 +458,8 @@ orc_net *orc_create(const orc_params *P, uint64_t seed) {
   net->ring = (int32_t *)calloc(N * (size_t)net->D, sizeof(int32_t));
   net->row_key = (uint32_t **)calloc(N, sizeof(uint32_t *));
   net->row_w = (float **)calloc(N, sizeof(float *));
+  net->row_threads = 1;
+  net->keep_rows = 1;
   /* initial membrane potential uniform on [0, V_theta) from stream 2 */
   for (int32_t n = 0; n < net->N; ++n) {
     uint32_t r[4];
@@ -440,6 +498,7 @@ static void orc_push_spike(orc_net *net, uint32_t t, uint32_t n) {
 int orc_run(orc_net *net, uint32_t steps) {
   int32_t N = net->N, M = net->M, D = net->D;
   uint32_t *spk = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)N);
+  uint32_t *miss = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)ORC_ROW_BATCH);
   for (uint32_t it = 0; it < steps; ++it) {
     uint32_t t = net->t;
     int32_t st = (int32_t)(t % (uint32_t)D);
@@ -470,22 +529,32 @@ int orc_run(orc_net *net, uint32_t steps) {
         orc_push_spike(net, t, (uint32_t)n);
       }
     }
-    /* delivery of this step's spikes in ascending source order */
-    for (int32_t i = 0; i < nsp; ++i) {
-      uint32_t s = spk[i];
-      orc_ensure_row(net, s);
-      const uint32_t *rk = net->row_key[s];
-      const float *rw = net->row_w[s];
-      for (int32_t j = 0; j < M; ++j) {
-        uint32_t d = rk[j] >> 24, tgt = rk[j] & 0xFFFFFFu;
-        int32_t sl = (int32_t)((t + d) % (uint32_t)D);
-        net->ring[(size_t)sl * (size_t)N + tgt] += orc_wfix(net, rw[j]);
+    /* delivery of this step's spikes in ascending source order, in batches
+     * whose missing rows are generated first */
+    for (int32_t b0 = 0; b0 < nsp; b0 += ORC_ROW_BATCH) {
+      int32_t b1 = b0 + ORC_ROW_BATCH < nsp ? b0 + ORC_ROW_BATCH : nsp;
+      int32_t nmiss = 0;
+      for (int32_t i = b0; i < b1; ++i)
+        if (!net->row_key[spk[i]]) miss[nmiss++] = spk[i];
+      if (nmiss) orc_make_rows(net, miss, nmiss);
+      for (int32_t i = b0; i < b1; ++i) {
+        uint32_t s = spk[i];
+        const uint32_t *rk = net->row_key[s];
+        const float *rw = net->row_w[s];
+        for (int32_t j = 0; j < M; ++j) {
+          uint32_t d = rk[j] >> 24, tgt = rk[j] & 0xFFFFFFu;
+          int32_t sl = (int32_t)((t + d) % (uint32_t)D);
+          net->ring[(size_t)sl * (size_t)N + tgt] += orc_wfix(net, rw[j]);
+        }
       }
+      if (!net->keep_rows)
+        for (int32_t i = b0; i < b1; ++i) orc_drop_row(net, spk[i]);
     }
     net->n_spikes += (uint64_t)nsp;
     net->n_rec_events += (uint64_t)nsp * (uint64_t)M;
     net->t = t + 1;
   }
+  free(miss);
   free(spk);
   return 0;
 }

@@ -482,9 +482,16 @@ __device__ bool deliver_items(const NetDev &nd, WarpStage &ws, uint32_t chunk, u
     bool got = mbar_wait_bounded(bar, ph, nd.wait_limit);
     got = __all_sync(0xFFFFFFFFu, got);
     if (!got) {
+      // drain the copies in flight (each with the default limit), keeping the
+      // phases in step with the barriers; the caller stops using the stage
       if (leader) atomicOr(&nd.rec->status, kStatusTimeout);
-      mbar_wait_bounded(bar, ph, kDefaultWaitLimit);
-      if (nxt < n_items) mbar_wait_bounded(b ? ws.bar0 : ws.bar1, b ? ws.ph0 : ws.ph1, kDefaultWaitLimit);
+      if (mbar_wait_bounded(bar, ph, kDefaultWaitLimit)) {
+        if (b) ws.ph1 ^= 1u; else ws.ph0 ^= 1u;
+      }
+      if (nxt < n_items && mbar_wait_bounded(b ? ws.bar0 : ws.bar1, b ? ws.ph0 : ws.ph1, kDefaultWaitLimit)) {
+        if (b) ws.ph0 ^= 1u; else ws.ph1 ^= 1u;
+      }
+      __syncwarp();
       return false;
     }
     if (b) ws.ph1 ^= 1u; else ws.ph0 ^= 1u;
@@ -797,18 +804,23 @@ __global__ void __launch_bounds__(512) k_fused(const __grid_constant__ FusedTabl
   __shared__ uint64_t s_bars[32];
   __shared__ uint32_t s_count;
   __shared__ uint32_t s_net;
+  __shared__ uint32_t s_abort;
   const uint32_t npi = 4u * blockDim.x;
   uint32_t *s_ids = reinterpret_cast<uint32_t *>(smem);
   uint8_t *stage_base = smem + (size_t)npi * 4u;
   const uint32_t warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   WarpStage ws;
   init_stage(ws, stage_base + (size_t)warp * 2u * kFusedCap * 8u, s_bars + 2 * warp, kFusedCap);
-  if (threadIdx.x == 0) s_net = 0xFFFFFFFFu;
+  if (threadIdx.x == 0) {
+    s_net = 0xFFFFFFFFu;
+    s_abort = 0u;
+  }
   bool waited = false;
   const uint32_t n_items = *tab.n_items;
   for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
     const FusedItem item = tab.items[it];
     __syncthreads();   // the previous item is done with shared memory
+    if (s_abort) break;   // a bounded wait gave up: no further copies into the stages
     if (s_net != item.net) {
       const uint32_t *src = reinterpret_cast<const uint32_t *>(tab.nets + item.net);
       uint32_t *dst = reinterpret_cast<uint32_t *>(&nd);
@@ -837,7 +849,9 @@ __global__ void __launch_bounds__(512) k_fused(const __grid_constant__ FusedTabl
     const uint32_t cnt = s_count;
     if (cnt == 0) continue;
     const uint32_t nch = (nd.M_pad + tab.chunk - 1u) / tab.chunk;
-    deliver_items(nd, ws, tab.chunk, warp, nw, cnt * nch, t % nd.D, [&](uint32_t s) { return s_ids[s]; });
+    if (!deliver_items(nd, ws, tab.chunk, warp, nw, cnt * nch, t % nd.D, [&](uint32_t s) { return s_ids[s]; }) &&
+        lane_id() == 0)
+      s_abort = 1u;
   }
   if (!waited) {
     pdl_wait();

@@ -71,6 +71,12 @@ extern "C" int snn_build_rows_static(const snn_params *p, uint64_t seed, void *r
   const uint32_t M_pad = (M + 7u) / 8u * 8u;
   const uint32_t row_bytes = M_pad * 4u + M_pad * (p->record_format == SNN_REC_I16 ? 2u : 4u);
   const size_t need = (size_t)N * row_bytes;
+  // The size query also looks up the scratch array's device address (which
+  // loads this module and places the array on the device), so that a caller
+  // can make it before reserving the rest of its device memory.
+  void *scratch = nullptr;
+  rc = scratch_address(&scratch);
+  if (rc) return rc;
   if (!rows_out) {           // size query
     *rows_bytes = need;
     return SNN_OK;
@@ -80,12 +86,16 @@ extern "C" int snn_build_rows_static(const snn_params *p, uint64_t seed, void *r
     return snn_fail(SNN_ERR_BUFFER, "rows_out holds fewer than N * row_bytes bytes");
   }
   if (reinterpret_cast<uintptr_t>(rows_out) % 16 != 0) return snn_fail(SNN_ERR_ARG, "rows_out must be 16-byte aligned");
-  void *scratch = nullptr;
-  rc = scratch_address(&scratch);
-  if (rc) return rc;
-  cudaError_t e = prepare_kernels();
-  if (e != cudaSuccess) return snn_fail(SNN_ERR_CUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  // The table uploads below read host vectors that are freed on return: a
+  // captured copy node would read them again at every replay.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess) return snn_fail(SNN_ERR_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
+  if (cap != cudaStreamCaptureStatusNone)
+    return snn_fail(SNN_ERR_ARG, "snn_build_rows_static must not be called on a capturing stream");
+  e = prepare_kernels();
+  if (e != cudaSuccess) return snn_fail(SNN_ERR_CUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
 
   // host tables: module thresholds and Gaussian quantiles
   std::vector<uint32_t> cdf;

@@ -42,6 +42,7 @@ class Result:
     spike_ids: np.ndarray
     rates: np.ndarray
     stats: dict
+    state: tuple | None = None          # final (V, c, refractory steps) when the server keeps states
 
     @property
     def latency_s(self) -> float:
@@ -63,6 +64,7 @@ class Server:
     chunk_steps: int = 1000                 # steps between admission points
     max_active: int = 1024
     realtime: bool = True                   # arrivals on the wall clock; else on completed chunks
+    keep_state: bool = False                # return each network's final neuron state with its result
     _queue: list = field(default_factory=list)
     _next_rid: int = 0
 
@@ -121,9 +123,10 @@ class Server:
                 st, ids = a.net.spikes()
                 rates = a.net.rates()
                 stats = a.net.stats()
+                state = a.net.state() if self.keep_state else None
                 events += stats["spikes"] * (a.net.M + EQUIV_PER_SPIKE_EXTRA)
                 results.append(Result(a.req.rid, a.req.arrival_s, a.admitted_s, t_done, a.req.steps, st, ids,
-                                      rates, stats))
+                                      rates, stats, state))
                 a.net.close()
                 ledger -= a.bytes
         wall = time.perf_counter() - t_start

@@ -521,3 +521,55 @@ def test_external_drive_compound_poisson_cumulants(oracle_mod):
         assert abs(x.mean() - k[0]) < 5 * se1, (x.mean(), k[0])
         assert abs(m2 - k[1]) < 5 * se2, (m2, k[1])
         assert abs(m3 - k[2]) < 5 * se3, (m3, k[2])
+
+
+# ---------------------------------------------------------------------------
+# Initial state (the paper does not state one; read as V0 uniform on [0, V_th))
+# ---------------------------------------------------------------------------
+def test_initial_state_uniform_per_population(oracle_mod):
+    """V0 of every neuron is uniform on [0, V_th) of its own population, on a
+    grid of 2^-24 V_th (a 24-bit uniform), independent from neuron to neuron
+    and independent of the draws the other random streams make (construction,
+    external drive, extra external events); c0 = 0 and no neuron starts
+    refractory.  Distinct thresholds per population catch a wrong population
+    lookup, the 24-bit grid and the range catch a wrong shift, neighbour
+    correlations and repeated values catch a counter shared by several neurons,
+    and the cross-stream correlations catch V0 taken from another stream's
+    draw.  Which of the unused streams V0 takes is a contract detail that only
+    the GPU parity tests check."""
+    p = W.base_params(4, 4, 1.0, "AW")
+    p["V_th"] = [20.0, 17.0, 13.0]
+    seed = 0x5EED0000ABCD
+    net = oracle_mod.OracleNet(p, seed)
+    V, c, ref = net.state()
+    assert np.all(c == 0.0) and np.all(ref == 0)
+    local = np.arange(net.N) % W.K
+    pop = np.where(local < 250, 0, np.where(local < 1000, 1, 2))
+    vth = np.array(p["V_th"], np.float32)[pop]
+    assert np.all(V >= 0.0) and np.all(V < vth)
+    # the 24-bit grid: V0 = fl(V_th * k * 2^-24) for an integer k < 2^24
+    k = np.rint(V.astype(np.float64) / vth.astype(np.float64) * 2.0 ** 24).astype(np.int64)
+    assert np.all((k >= 0) & (k < 2 ** 24))
+    assert np.array_equal((vth * (k.astype(np.float32) * np.float32(2.0 ** -24))).astype(np.float32), V)
+    assert k.max() > 0.999 * 2 ** 24 and k.min() < 0.001 * 2 ** 24
+    u = k / 2.0 ** 24
+    for q in range(3):
+        assert scipy.stats.kstest(u[pop == q], "uniform").pvalue > 1e-3, q
+    # independence across neurons
+    n = u.size
+    for lag in (1, 2, 3, 4, 1250):
+        r = np.corrcoef(u[:-lag], u[lag:])[0, 1]
+        assert abs(r) < 4.5 / math.sqrt(n), (lag, r)
+    assert np.unique(k).size > n - 60      # ~N^2 / 2^25 = 12 coincidences expected
+    # independent of the other streams' draws at the same counters
+    k0, k1 = seed & 0xFFFFFFFF, seed >> 32
+    idx = np.arange(0, n, 7)
+    others = {
+        "construction": [oracle_mod.philox([i, 0, 0, 0], k0, k1)[0] for i in idx],
+        "drive": [oracle_mod.philox([i // 4, 0, 1, 0], k0, k1)[i % 4] for i in idx],
+        "extra events": [oracle_mod.philox([i, 0, 3, 0], k0, k1)[0] for i in idx],
+    }
+    for name, words in others.items():
+        w = (np.array(words, np.uint64) >> 8).astype(np.float64) / 2.0 ** 24
+        r = np.corrcoef(w, u[idx])[0, 1]
+        assert abs(r) < 4.5 / math.sqrt(idx.size), (name, r)

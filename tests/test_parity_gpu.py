@@ -4,12 +4,14 @@ Spike rasters, synapse rows, rate counts, counters and the refractory state are
 integer results and must match bit for bit.  V and c are binary32 results of
 the same operation sequence on both sides; the bar is |a - b| <= 1e-6 * max(1, |b|)
 (identical bits are expected: both sides round every operation once, with no
-fused multiply-add).
+fused multiply-add).  The benchmarked grids at length are in
+test_long_parity_gpu.py.
 """
 import numpy as np
 import pytest
 
 import workloads as W
+from parity import assert_same, gpu_results, oracle_results
 
 pytestmark = pytest.mark.gpu
 
@@ -31,22 +33,7 @@ def _oracle(oracle_mod, params, seed, steps):
 
 
 def _assert_same_run(g, o, steps):
-    gt, gi = g.spikes()
-    ot, oi = o.raster()
-    assert len(gt) == len(ot), (len(gt), len(ot))
-    assert np.array_equal(gt, ot) and np.array_equal(gi, oi)
-    gr, orr = g.rates(), o.rates()
-    assert np.array_equal(gr, orr)
-    gV, gc, gref = g.state()
-    oV, oc, oref = o.state()
-    assert np.array_equal(gref, oref)
-    tolV = 1e-6 * np.maximum(1.0, np.abs(oV))
-    tolc = 1e-6 * np.maximum(1.0, np.abs(oc))
-    assert np.all(np.abs(gV - oV) <= tolV)
-    assert np.all(np.abs(gc - oc) <= tolc)
-    gs, oc_ = g.stats(), o.counters()
-    assert gs["spikes"] == oc_["spikes"] and gs["ext_events"] == oc_["ext_events"]
-    assert gs["rec_events"] == oc_["rec_events"] and gs["t"] == steps
+    assert_same(gpu_results(g), oracle_results(o), steps)
 
 
 # ---------------------------------------------------------------------------
@@ -176,18 +163,6 @@ def test_run_table_s1_pure_kernel(snn, oracle_mod):
     g.run(800)
     o = _oracle(oracle_mod, p, 3, 800)
     _assert_same_run(g, o, 800)
-
-
-def test_run_24x24_window(snn, oracle_mod):
-    """24x24 AW grid at full size: the first 150 steps, both paths."""
-    p = W.base_params(24, 24, 1.0, "AW")
-    o = _oracle(oracle_mod, p, 1, 150)
-    for path in (0, 1):
-        g = snn.Network(p, 1)
-        g.launch = {"path": path}
-        g.run(150)
-        _assert_same_run(g, o, 150)
-        g.close()
 
 
 def test_zero_steps_and_no_spike_input(snn, oracle_mod):
@@ -358,14 +333,12 @@ def test_wait_limit_zero_reports_timeout(snn):
 
 
 @pytest.mark.parametrize("fmt", [W.REC_F32, W.REC_I16])
-def test_run_64x64_first_steps(snn, oracle_mod, fmt):
-    """64x64 grid (5.12M neurons, 5.76G synapses) at full size: the first steps
-    (the oracle builds only the rows of neurons that fire) and sampled rows."""
+def test_rows_bit_exact_64x64_sample(snn, oracle_mod, fmt):
+    """64x64 grid (5.12M neurons, 5.76G synapses): sampled rows, both formats
+    (whole runs of this grid are compared in test_long_parity_gpu.py)."""
     p = W.base_params(64, 64, 1.0, "AW", record_format=fmt)
     g = snn.Network(p, 1)
-    g.run(4)
-    o = _oracle(oracle_mod, p, 1, 4)
-    _assert_same_run(g, o, 4)
+    o = oracle_mod.OracleNet(p, 1)
     rng = np.random.default_rng(2)
     for s in np.concatenate([[0, g.N - 1], rng.integers(0, g.N, 20)]):
         gk, gw = g.row(int(s))

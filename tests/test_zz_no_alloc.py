@@ -48,12 +48,12 @@ def _build_static(snn, torch, p, seed):
     return buf.cpu().numpy()
 
 
-def _compare(snn, p, seed, host_rows):
+def _compare(snn, p, seed, host_rows, sources=None):
     net = snn.Network(p, seed)
     m_pad, rb = _row_bytes(p)
     M = p["out_degree"]
     rows = host_rows.reshape(net.N, rb)
-    for s in range(net.N):
+    for s in (range(net.N) if sources is None else sources):
         keys, w = net.row(s)
         got_keys = rows[s, :M * 4].view(np.uint32)
         assert np.array_equal(got_keys, keys), s
@@ -87,3 +87,56 @@ def test_static_scratch_limits(env):
     assert lib.snn_build_rows_static(ctypes.byref(small), 1, ctypes.c_void_p(buf.data_ptr()), ctypes.byref(short),
                                      None) == -5
     assert short.value == need.value
+
+
+def test_static_scratch_at_its_module_limit(env):
+    """Exactly 1024 modules (32x32, the most the static scratch serves): the
+    threshold table fills its whole region and the Gaussian table sits right
+    behind it.  Sampled rows, the first and the last source included."""
+    snn, torch = env
+    p = W.base_params(32, 32, 1.0, record_format=W.REC_I16)
+    p["out_degree"] = 8
+    rows = _build_static(snn, torch, p, 3)
+    n = 32 * 32 * W.K
+    rng = np.random.default_rng(5)
+    sample = np.unique(np.concatenate([[0, 1, 1249, 1250, n // 2, n - 1251, n - 1],
+                                       rng.integers(0, n, 200)]))
+    _compare(snn, p, 3, rows, sample)
+
+
+def test_static_scratch_refuses_a_capturing_stream(env):
+    """The tables are uploaded from host memory that the call frees on return,
+    so a call on a stream being captured into a graph is refused."""
+    import os
+    snn, torch = env
+    lib = snn.lib()
+    cudart = None
+    for cand in (os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "lib64", "libcudart.so"),
+                 "libcudart.so"):
+        try:
+            cudart = ctypes.CDLL(cand)
+            break
+        except OSError:
+            continue
+    if cudart is None:
+        pytest.skip("libcudart.so not found")
+    p = W.base_params(2, 2, 1.0)
+    pp = snn.make_params(p)
+    need = ctypes.c_size_t(0)
+    assert lib.snn_build_rows_static(ctypes.byref(pp), 1, None, ctypes.byref(need), None) == 0   # warm-up
+    buf = torch.empty(need.value, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    capture_thread_local = 1                               # cudaStreamCaptureModeThreadLocal
+    assert cudart.cudaStreamBeginCapture(sp, capture_thread_local) == 0
+    have = ctypes.c_size_t(need.value)
+    rc = lib.snn_build_rows_static(ctypes.byref(pp), 1, ctypes.c_void_p(buf.data_ptr()), ctypes.byref(have), sp)
+    graph = ctypes.c_void_p()
+    assert cudart.cudaStreamEndCapture(sp, ctypes.byref(graph)) == 0
+    if graph.value:
+        cudart.cudaGraphDestroy(graph)
+    assert rc == -1, lib.snn_last_error()
+    # the stream is usable afterwards
+    rc = lib.snn_build_rows_static(ctypes.byref(pp), 1, ctypes.c_void_p(buf.data_ptr()), ctypes.byref(have), sp)
+    assert rc == 0, lib.snn_last_error()
+    stream.synchronize()
