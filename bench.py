@@ -79,7 +79,7 @@ def parse_args():
     ap.add_argument("--update-block", type=int, default=128)
     ap.add_argument("--update-groups", type=int, default=1)
     ap.add_argument("--deliver-warps", type=int, default=4)
-    ap.add_argument("--deliver-chunk", type=int, default=192)
+    ap.add_argument("--deliver-lanes", type=int, default=8)
     ap.add_argument("--deliver-blocks", type=int, default=8)
     ap.add_argument("--l2-persist", type=int, choices=[0, 1], default=1,
                     help="persisting L2 window (profile mode, and grid mode with --no-tune)")
@@ -597,7 +597,7 @@ def run_batch_mode(args, dist: Dist):
                                    "steps": args.plain_steps},
         "speedup": (ev_batch / t_batch) / (ev_plain / t_plain),
         "identical_rasters": f"{same}/{len(nets)} networks (first {warm} steps)",
-        "fused_launch": {k: tuned[k] for k in ("fused_block", "fused_items_per_sm", "deliver_chunk", "window_steps")},
+        "fused_launch": {k: tuned[k] for k in ("fused_block", "fused_items_per_sm", "deliver_lanes", "window_steps")},
         "timing": f"both forms timed after the first {warm} steps of each network",
         "cpu_baseline": cpu,
         "build_seconds": build_s, "clocks": clocks,
@@ -787,7 +787,7 @@ def run_profile_mode(args, dist: Dist):
     net = snn.Network(W.base_params(args.grid, args.grid, 1.0, args.regime, record_format=fmt), 1)
     net.launch = {"path": args.path, "window_steps": args.window, "update_block": args.update_block,
                   "update_groups": args.update_groups, "deliver_warps": args.deliver_warps,
-                  "deliver_chunk": args.deliver_chunk, "l2_persist": args.l2_persist,
+                  "deliver_lanes": args.deliver_lanes, "l2_persist": args.l2_persist,
                   "deliver_blocks": args.deliver_blocks}
     net.run(args.warm_steps)
     net.run(args.run_steps)

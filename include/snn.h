@@ -39,7 +39,6 @@ extern "C" {
 #define SNN_ERR_ARG -1       /* invalid argument or parameter set */
 #define SNN_ERR_OOM -2       /* device or host allocation failed */
 #define SNN_ERR_CUDA -3      /* CUDA runtime error or no device */
-#define SNN_ERR_TIMEOUT -4   /* a bounded device wait gave up; results of the call are invalid */
 #define SNN_ERR_BUFFER -5    /* caller buffer too small; *n_out holds the required count */
 #define SNN_ERR_LIMIT -6     /* size beyond an implementation limit (e.g. N >= 2^24 neurons) */
 #define SNN_ERR_STATE -7     /* call not valid in the current state */
@@ -100,22 +99,21 @@ typedef struct snn_stats {
 typedef struct snn_launch {
   int32_t path;            /* 0 = two kernels per step (update, deliver); 1 = fused step kernel */
   int32_t update_block;    /* threads per update block: 64 (update_groups 1 only), 128, 256 or 512 */
-  int32_t deliver_warps;   /* warps per deliver block: 1..8 */
+  int32_t deliver_warps;   /* warps per delivery block: 1..8 (a block delivers one module at a time) */
   int32_t fused_block;     /* threads per fused-step block: 128..512 */
   int32_t fused_items_per_sm; /* fused blocks per SM to launch (1..32, capped by occupancy) */
   int32_t window_steps;    /* steps per captured CUDA graph (1..4096) */
-  int32_t deliver_chunk;   /* synapse records per delivery work item, multiple of 8
-                              (two-kernel path <= 1152, fused path <= 256) */
+  int32_t deliver_lanes;   /* lanes that share one (spike, delay) segment of records: 4, 8, 16, 32 */
   int32_t update_groups;   /* groups of 4 neurons per update thread: 1, 2 or 4
                               (512-thread blocks: 1 or 2) */
-  int32_t l2_persist;      /* two-kernel path: 1 = the neuron state and delay ring are
+  int32_t l2_persist;      /* two-kernel path: 1 = the neuron state and input buffers are
                               given a persisting L2 access-policy window (the CUDA
                               context's persisting set-aside is raised to the device
                               maximum while any such network lives, then restored);
                               0 = normal caching */
-  int32_t deliver_blocks;  /* deliver blocks per SM: 1..32 (the grid is SMs x deliver_blocks;
-                              each warp stages 2 x deliver_chunk records in shared memory,
-                              at most 200 KB per block) */
+  int32_t deliver_blocks;  /* delivery blocks per SM: 1..32 (the grid is min(modules,
+                              SMs x deliver_blocks); blocks take several modules each
+                              when the grid has more modules than that) */
 } snn_launch;
 
 typedef void *(*snn_alloc_fn)(size_t bytes, void *ctx);
@@ -128,13 +126,16 @@ typedef void (*snn_free_fn)(void *ptr, void *ctx);
 int snn_set_allocator(snn_alloc_fn alloc, snn_free_fn free_fn, void *ctx);
 
 /* Device bytes a network with these parameters will hold once built
- * (synapse records, neuron state, delay ring, tables, recording buffers). */
+ * (synapse records and their delay-group table, neuron state, input buffers,
+ * spike history of the last n_delay + 1 steps, tables, recording buffers). */
 int snn_footprint(const snn_params *p, size_t *bytes_out);
 
 /* Build a network on the device (Sec. 2.1 initialisation; Eq. 1 connectivity,
  * Sec. 2.2 efficacies).  Synapse j of source neuron s is a pure function of
- * (seed, s, j) drawn from Philox4x32-10, each outgoing row is stored ordered
- * by delay (ties in draw order), and the initial V is uniform on [0, V_th).
+ * (seed, s, j) drawn from Philox4x32-10, each outgoing row is stored grouped
+ * by delay (the paper's delay-ordered synapse lists, Sec. 2.1) and by target
+ * within a delay (ties in draw order), with the end of each delay group kept
+ * in a table, and the initial V is uniform on [0, V_th).
  * `cuda_stream` (a cudaStream_t, or NULL for the legacy default stream) is the
  * stream every later call of this network is ordered on.  The call returns
  * when the network is ready.  Errors: SNN_ERR_ARG (bad parameters),
@@ -142,10 +143,11 @@ int snn_footprint(const snn_params *p, size_t *bytes_out);
 int snn_build_network(const snn_params *p, uint64_t seed, void *cuda_stream, snn_handle *out);
 
 /* Advance the network by `steps` time steps (Eq. 2 update with Poisson drive,
- * spike detection, delivery of each spike's row into the delay ring) and
- * record spikes and rate counts.  Returns after the steps completed and their
- * records reached host memory.  Errors: SNN_ERR_TIMEOUT (a bounded wait in a
- * kernel gave up), SNN_ERR_CUDA. */
+ * spike detection, delivery of each spike's records to their targets d steps
+ * later, Sec. 2.1.1) and record spikes and rate counts (Sec. 2.3).  Returns
+ * after the steps completed and their records reached host memory.  Errors:
+ * SNN_ERR_LIMIT (spike record window overflowed: cannot happen with a
+ * refractory period of at least one step), SNN_ERR_CUDA. */
 int snn_run(snn_handle h, uint64_t steps);
 
 /* Advance n networks together by steps[i] each with one fused kernel per time
@@ -251,11 +253,6 @@ void snn_free(snn_handle h);
 /* Message of the last failed call on this thread ("" if none). */
 const char *snn_last_error(void);
 
-/* Testing aid: iteration limit of the kernels' bounded waits on their own
- * asynchronous copies (default about one second).  With 0 every wait gives up
- * at once: the kernel records SNN_ERR_TIMEOUT, waits with the default limit
- * for its copies in flight, and returns; the network is then invalid. */
-int snn_debug_set_wait_limit(snn_handle h, uint32_t iterations);
 
 #ifdef __cplusplus
 }

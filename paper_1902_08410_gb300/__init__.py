@@ -16,7 +16,7 @@ from . import _native
 from ._native import SnnLaunch, SnnParams, SnnStats
 
 SNN_OK = 0
-ERRORS = {-1: "SNN_ERR_ARG", -2: "SNN_ERR_OOM", -3: "SNN_ERR_CUDA", -4: "SNN_ERR_TIMEOUT",
+ERRORS = {-1: "SNN_ERR_ARG", -2: "SNN_ERR_OOM", -3: "SNN_ERR_CUDA",
           -5: "SNN_ERR_BUFFER", -6: "SNN_ERR_LIMIT", -7: "SNN_ERR_STATE"}
 REC_F32 = 0
 REC_I16 = 1
@@ -220,8 +220,6 @@ class Network:
         _check(self._lib.snn_time_kernels(self._h, int(steps), out))
         return {"update_ms": out[0], "deliver_ms": out[1], "step_ms": out[2]}
 
-    def set_wait_limit(self, iterations: int) -> None:
-        _check(self._lib.snn_debug_set_wait_limit(self._h, int(iterations)))
 
 
 def run_concurrent(nets, steps) -> None:

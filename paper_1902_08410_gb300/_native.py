@@ -94,7 +94,7 @@ class SnnStats(ctypes.Structure):
 class SnnLaunch(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("update_block", ctypes.c_int32), ("deliver_warps", ctypes.c_int32),
                 ("fused_block", ctypes.c_int32), ("fused_items_per_sm", ctypes.c_int32),
-                ("window_steps", ctypes.c_int32), ("deliver_chunk", ctypes.c_int32),
+                ("window_steps", ctypes.c_int32), ("deliver_lanes", ctypes.c_int32),
                 ("update_groups", ctypes.c_int32), ("l2_persist", ctypes.c_int32),
                 ("deliver_blocks", ctypes.c_int32)]
 
@@ -106,7 +106,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 EXPORTS = ["snn_set_allocator", "snn_footprint", "snn_build_network", "snn_run", "snn_run_batch",
            "snn_read_spikes", "snn_rates", "snn_read_state", "snn_read_row", "snn_get_stats",
            "snn_get_launch", "snn_set_launch", "snn_autotune", "snn_free", "snn_last_error",
-           "snn_debug_set_wait_limit", "snn_time_kernels", "snn_build_rows_static", "snn_run_concurrent",
+           "snn_time_kernels", "snn_build_rows_static", "snn_run_concurrent",
            "snn_autotune_batch"]
 
 _lib = None
@@ -142,7 +142,6 @@ def load(build_if_needed: bool = True):
         "snn_autotune_batch": ([P(vp), i32, u32], ctypes.c_int),
         "snn_free": ([vp], None),
         "snn_last_error": ([], ctypes.c_char_p),
-        "snn_debug_set_wait_limit": ([vp, u32], ctypes.c_int),
         "snn_time_kernels": ([vp, u32, P(ctypes.c_double)], ctypes.c_int),
         "snn_build_rows_static": ([P(SnnParams), u64, vp, P(sz), vp], ctypes.c_int),
     }

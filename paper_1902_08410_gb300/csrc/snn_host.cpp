@@ -257,17 +257,19 @@ void build_inputs(const snn_params &p, BuildDev &bd) {
 // ---------------------------------------------------------------------------
 // network object
 // ---------------------------------------------------------------------------
-// Device arena of one network, in this order: V, c, ref, ring (the state a run
-// modifies), synapse rows, amplitude table, two windows, two recording blocks
+// Device arena of one network, in this order: V, c, ref, the input buffers
+// acc_loc[2] and acc_rem[2], the per-module spike counts and spike history of
+// the last n_delay + 1 steps (everything a run modifies), synapse rows, their
+// delay-group table, amplitude table, two windows, two recording blocks
 // (header, external-event slots, rate window: one contiguous copy per window),
 // two raster entry buffers.  Windows alternate between the two buffer sets, so
 // the host drains one window's records while the GPU runs the next.
 struct Layout {
-  size_t off_V, off_c, off_ref, off_ring, off_rows, off_amp;
+  size_t off_V, off_c, off_ref, off_acc_loc, off_acc_rem, off_hcnt, off_hist, off_rows, off_offs, off_amp;
   size_t off_win[2], off_rec[2], off_ext[2], off_rates[2], off_entries[2];
   size_t rec_block;   // bytes of one recording block
   size_t total;
-  uint32_t N, N_pad, G, M, M_pad, D, row_bytes;
+  uint32_t N, N_pad, G, M, M_pad, D, row_bytes, os;
   uint32_t window, rates_bins, rec_cap, n_ext_slots;
 };
 
@@ -307,6 +309,7 @@ static Layout make_layout(const snn_params &p) {
   L.M_pad = (uint32_t)align_up(L.M, 8);
   L.D = (uint32_t)p.n_delay + 1u;
   L.row_bytes = L.M_pad * 4u + L.M_pad * (p.record_format == SNN_REC_I16 ? 2u : 4u);
+  L.os = offs_stride((uint32_t)p.n_delay);
   L.n_ext_slots = L.N_pad / 128u;
   int narp_min = 255;
   for (int q = 0; q < 3; ++q)
@@ -329,8 +332,12 @@ static Layout make_layout(const snn_params &p) {
   L.off_V = take((size_t)L.N_pad * 4);
   L.off_c = take((size_t)L.N_pad * 4);
   L.off_ref = take((size_t)L.N_pad);
-  L.off_ring = take((size_t)L.D * L.N_pad * 4);
+  L.off_acc_loc = take((size_t)2 * L.N_pad * 4);
+  L.off_acc_rem = take((size_t)2 * L.N_pad * 4);
+  L.off_hcnt = take((size_t)L.D * L.G * 4);
+  L.off_hist = take((size_t)L.D * L.N * 4);
   L.off_rows = take((size_t)L.N * L.row_bytes);
+  L.off_offs = take((size_t)L.N * L.os * 2);
   L.off_amp = take((size_t)kNPop * kZTab * 4);
   for (int b = 0; b < 2; ++b) L.off_win[b] = take(sizeof(NetWin));
   const size_t ext_at = 256;
@@ -364,9 +371,7 @@ struct snn_net {
   cudaGraphExec_t exec[2] = {nullptr, nullptr};   // one graph per buffer set
   uint32_t exec_window = 0;
   snn_launch exec_cfg{};
-  uint32_t exec_wait_limit = 0;
   float exec_l2_ratio = -1.0f;       // hit ratio baked into the captured graphs
-  uint32_t wait_limit = 1u << 22;
   // host records
   uint64_t t = 0;
   std::vector<unsigned long long> raster;   // (step << 32 | id), non-decreasing in step
@@ -419,10 +424,10 @@ static void l2_release(snn_net *h) {
   }
 }
 
-// Bytes of the persisting window at the start of the arena: V, c, ref and the
-// ring when they fit the set-aside together (the ring then stays in L2 for the
-// scattered reductions), else V, c and ref alone (a ring larger than L2
-// misses on most reductions whatever its policy; the neuron state still fits).
+// Bytes of the persisting window at the start of the arena: V, c, ref, the
+// input buffers and the spike counts when they fit the set-aside together,
+// else V, c and ref alone.  The spike history (sparse: only the ids of recent
+// spikes are touched) is never part of it.
 static size_t l2_window_bytes(const snn_net *h) {
   int dev = 0, max_win = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -430,7 +435,7 @@ static size_t l2_window_bytes(const snn_net *h) {
     cudaGetLastError();
     return 0;
   }
-  const size_t all = h->L.off_rows, state = h->L.off_ring;
+  const size_t all = h->L.off_hist, state = h->L.off_acc_loc;
   return std::min<size_t>(all <= g_l2_setaside ? all : state, (size_t)max_win);
 }
 
@@ -457,6 +462,10 @@ static int sm_count_cached() {
   return v;
 }
 
+// Delivery grid: one block per module, at most deliver_blocks per SM (blocks
+// then take several modules each).
+static int deliver_grid(const snn_net *h);
+
 static void default_launch(snn_net *h) {
   h->cfg.path = 0;
   h->cfg.update_block = 128;
@@ -464,7 +473,7 @@ static void default_launch(snn_net *h) {
   h->cfg.fused_block = 128;
   h->cfg.fused_items_per_sm = 8;
   h->cfg.window_steps = (int32_t)h->L.window;
-  h->cfg.deliver_chunk = 192;
+  h->cfg.deliver_lanes = 8;
   h->cfg.update_groups = 1;
   h->cfg.l2_persist = 1;
   h->cfg.deliver_blocks = 8;
@@ -476,6 +485,11 @@ extern "C" int snn_footprint(const snn_params *p, size_t *bytes_out) {
   if (rc) return rc;
   *bytes_out = make_layout(*p).total;
   return SNN_OK;
+}
+
+static int deliver_grid(const snn_net *h) {
+  const int sms = h->sm_count > 0 ? h->sm_count : 148;
+  return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->L.G, (int64_t)sms * h->cfg.deliver_blocks));
 }
 
 static void free_net(snn_net *h) {
@@ -522,7 +536,8 @@ static void fill_descriptor(snn_net *h) {
   d.slot = 0;
   d.rec_cap = L.rec_cap;
   d.rates_bins = L.rates_bins;
-  d.wait_limit = h->wait_limit;
+  d.n_delay = (uint32_t)h->p.n_delay;
+  d.os = L.os;
   for (int q = 0; q < 3; ++q) {
     const PopTables t = pop_tables(h->p, q);
     d.pvv[q] = t.pvv;
@@ -538,8 +553,12 @@ static void fill_descriptor(snn_net *h) {
   d.V = reinterpret_cast<float *>(base + L.off_V);
   d.c = reinterpret_cast<float *>(base + L.off_c);
   d.ref = base + L.off_ref;
-  d.ring = reinterpret_cast<int32_t *>(base + L.off_ring);
+  d.acc_loc = reinterpret_cast<int32_t *>(base + L.off_acc_loc);
+  d.acc_rem = reinterpret_cast<int32_t *>(base + L.off_acc_rem);
+  d.hcnt = reinterpret_cast<uint32_t *>(base + L.off_hcnt);
+  d.hist = reinterpret_cast<uint32_t *>(base + L.off_hist);
   d.rows = base + L.off_rows;
+  d.offs = reinterpret_cast<const uint16_t *>(base + L.off_offs);
   d.amp = reinterpret_cast<const int32_t *>(base + L.off_amp);
   set_buffers(d, h, 0);
 }
@@ -558,7 +577,6 @@ static void set_buffers(NetDev &d, const snn_net *h, int b) {
 static NetDev descriptor(const snn_net *h, int b) {
   NetDev d = h->hd;
   set_buffers(d, h, b);
-  d.wait_limit = h->wait_limit;
   return d;
 }
 
@@ -629,7 +647,7 @@ extern "C" int snn_build_network(const snn_params *p, uint64_t seed, void *cuda_
   h->launches += 2;
   bd.cdf = d_cdf;
   bd.ztab = d_z;
-  CU_TRY(cudaMemsetAsync(base + L.off_ring, 0, (size_t)L.D * L.N_pad * 4, s));
+  CU_TRY(cudaMemsetAsync(base + L.off_acc_loc, 0, L.off_hist - L.off_acc_loc, s));   // inputs, spike counts
   CU_TRY(cudaMemsetAsync(base + L.off_win[0], 0, L.off_entries[0] - L.off_win[0], s));   // windows, blocks
   CU_TRY(cudaMallocHost(&h->pinned_win, 2 * sizeof(NetWin)));
   std::memset(h->pinned_win, 0, 2 * sizeof(NetWin));
@@ -649,18 +667,16 @@ static int capture_window(snn_net *h, uint32_t window) {
   L2Window l2;   // set-aside changes are not allowed while a capture is open
   int rc = l2_window(h, &l2);
   if (rc) return rc;
-  if (h->exec[0] && h->exec[1] && h->exec_window == window && h->exec_wait_limit == h->wait_limit &&
-      h->exec_l2_ratio == l2.hit_ratio && std::memcmp(&h->exec_cfg, &h->cfg, sizeof(snn_launch)) == 0)
+  if (h->exec[0] && h->exec[1] && h->exec_window == window && h->exec_l2_ratio == l2.hit_ratio &&
+      std::memcmp(&h->exec_cfg, &h->cfg, sizeof(snn_launch)) == 0)
     return SNN_OK;
   for (int b = 0; b < 2; ++b)
     if (h->exec[b]) {
       cudaGraphExecDestroy(h->exec[b]);
       h->exec[b] = nullptr;
     }
-  h->hd.wait_limit = h->wait_limit;
   const snn_launch &c = h->cfg;
   cudaStream_t cs = h->cap_stream;
-  const int sms = h->sm_count > 0 ? h->sm_count : 148;
   for (int b = 0; b < 2; ++b) {
     const NetDev d = descriptor(h, b);
     CU_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
@@ -668,7 +684,7 @@ static int capture_window(snn_net *h, uint32_t window) {
     for (uint32_t k = 0; k < window && err == cudaSuccess; ++k) {
       err = launch_update(d, k, c.update_block, c.update_groups, l2, cs);
       if (err == cudaSuccess)
-        err = launch_deliver(d, k, (uint32_t)c.deliver_chunk, c.deliver_warps, sms * c.deliver_blocks, l2, cs);
+        err = launch_deliver(d, k, (uint32_t)c.deliver_lanes, c.deliver_warps, deliver_grid(h), l2, cs);
     }
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(cs, &g);
@@ -683,7 +699,6 @@ static int capture_window(snn_net *h, uint32_t window) {
   }
   h->exec_window = window;
   h->exec_cfg = h->cfg;
-  h->exec_wait_limit = h->wait_limit;
   h->exec_l2_ratio = l2.hit_ratio;
   return SNN_OK;
 }
@@ -709,10 +724,6 @@ static int drain_copy_entries(snn_net *h, int b, cudaStream_t s, uint32_t *n_out
   uint8_t *base = static_cast<uint8_t *>(h->arena.p);
   const RecHeader *rh = reinterpret_cast<const RecHeader *>(pinned_block(h, b));
   *n_out = 0;
-  if (rh->status & kStatusTimeout) {
-    h->broken = true;
-    return fail(SNN_ERR_TIMEOUT, "a bounded wait on an asynchronous copy gave up; the network is invalid");
-  }
   if (rh->status & kStatusRasterOverflow) {
     h->broken = true;
     return fail(SNN_ERR_LIMIT, "spike record window overflowed");
@@ -914,7 +925,7 @@ struct BatchCtx {
   cudaStream_t cap_stream = nullptr, copy_stream = nullptr;
   cudaEvent_t ev_block[2] = {nullptr, nullptr};
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
-  uint32_t exec_window = 0, exec_items = 0, exec_chunk = 0;
+  uint32_t exec_window = 0, exec_items = 0, exec_lanes = 0;
   uint32_t pinned_count = 0;   // staging of the item count (copied before the replays)
   int exec_block = 0, exec_blocks = 0;
   void drop_graphs() {
@@ -949,7 +960,7 @@ static int run_fused(snn_net *const *hs, const uint64_t *steps, int32_t n) {
   const snn_launch &cfg = hs[0]->cfg;
   const int block = cfg.fused_block;
   const uint32_t npi = 4u * (uint32_t)block;
-  const uint32_t chunk = std::min<uint32_t>((uint32_t)cfg.deliver_chunk, max_fused_chunk_records());
+  const uint32_t lanes = (uint32_t)cfg.deliver_lanes;
   size_t n_items = 0;
   uint32_t window = 0xFFFFFFFFu;
   for (int i = 0; i < n; ++i) {
@@ -1004,8 +1015,14 @@ static int run_fused(snn_net *const *hs, const uint64_t *steps, int32_t n) {
   for (int i = 0; i < n; ++i)
     if (hs[i]->stream != s) CU_TRY(cudaStreamSynchronize(hs[i]->stream));
   size_t it = 0;
-  for (int i = 0; i < n; ++i)
-    for (uint32_t b = 0; b < hs[i]->L.N_pad; b += npi) B.pinned_items[it++] = FusedItem{(uint32_t)i, b};
+  for (int i = 0; i < n; ++i) {
+    // items of network i: consecutive neuron ranges; its modules are spread
+    // evenly over them (item j delivers modules [j G / I, (j + 1) G / I))
+    const uint64_t I = (hs[i]->L.N_pad + npi - 1) / npi, G = hs[i]->L.G;
+    for (uint64_t j = 0; j < I; ++j)
+      B.pinned_items[it++] = FusedItem{(uint32_t)i, (uint32_t)(j * npi), (uint32_t)(j * G / I),
+                                       (uint32_t)((j + 1) * G / I)};
+  }
   for (int b = 0; b < 2; ++b)
     for (int i = 0; i < n; ++i) {
       NetDev d = descriptor(hs[i], b);
@@ -1017,11 +1034,11 @@ static int run_fused(snn_net *const *hs, const uint64_t *steps, int32_t n) {
   const int per_sm = std::min(cfg.fused_items_per_sm, fused_blocks_per_sm(block));
   const int blocks = sms * per_sm;   // fixed grid: the same graphs serve any set of networks
   if (!B.exec[0] || !B.exec[1] || B.exec_window != window || B.exec_block != block || B.exec_blocks != blocks ||
-      B.exec_chunk != chunk) {
+      B.exec_lanes != lanes) {
     B.drop_graphs();
     for (int b = 0; b < 2; ++b) {
       FusedTable tab{static_cast<const NetDev *>(B.nets[b].p), static_cast<const FusedItem *>(B.items.p),
-                     static_cast<const uint32_t *>(B.n_items_dev.p), chunk};
+                     static_cast<const uint32_t *>(B.n_items_dev.p), lanes};
       CU_TRY(cudaStreamBeginCapture(B.cap_stream, cudaStreamCaptureModeThreadLocal));
       cudaError_t err = cudaSuccess;
       for (uint32_t k = 0; k < window && err == cudaSuccess; ++k)
@@ -1041,7 +1058,7 @@ static int run_fused(snn_net *const *hs, const uint64_t *steps, int32_t n) {
     B.exec_items = (uint32_t)n_items;
     B.exec_block = block;
     B.exec_blocks = blocks;
-    B.exec_chunk = chunk;
+    B.exec_lanes = lanes;
   }
   CU_TRY(cudaMemcpyAsync(B.items.p, B.pinned_items, n_items * sizeof(FusedItem), cudaMemcpyHostToDevice, s));
   B.pinned_count = (uint32_t)n_items;
@@ -1243,7 +1260,6 @@ extern "C" int snn_get_stats(snn_handle h, snn_stats *out) {
 static int capture_timing_graph(snn_net *h, uint32_t steps, const L2Window &l2, cudaEvent_t *ev,
                                 cudaGraphExec_t *out) {
   const NetDev d = descriptor(h, 0);
-  const int sms = h->sm_count > 0 ? h->sm_count : 148;
   cudaStream_t cs = h->cap_stream;
   CU_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   cudaError_t err = cudaSuccess;
@@ -1253,8 +1269,7 @@ static int capture_timing_graph(snn_net *h, uint32_t steps, const L2Window &l2, 
     if (ev && err == cudaSuccess) err = cudaEventRecordWithFlags(ev[4 * k + 1], cs, cudaEventRecordExternal);
     if (ev && err == cudaSuccess) err = cudaEventRecordWithFlags(ev[4 * k + 2], cs, cudaEventRecordExternal);
     if (err == cudaSuccess)
-      err = launch_deliver(d, k, (uint32_t)h->cfg.deliver_chunk, h->cfg.deliver_warps, sms * h->cfg.deliver_blocks, l2,
-                           cs);
+      err = launch_deliver(d, k, (uint32_t)h->cfg.deliver_lanes, h->cfg.deliver_warps, deliver_grid(h), l2, cs);
     if (ev && err == cudaSuccess) err = cudaEventRecordWithFlags(ev[4 * k + 3], cs, cudaEventRecordExternal);
   }
   cudaGraph_t g = nullptr;
@@ -1278,7 +1293,6 @@ extern "C" int snn_time_kernels(snn_handle h, uint32_t steps, double *ms_out) {
   const Layout &L = h->L;
   uint8_t *base = static_cast<uint8_t *>(h->arena.p);
   cudaStream_t s = h->stream;
-  h->hd.wait_limit = h->wait_limit;
   L2Window l2;
   int rc = l2_window(h, &l2);
   if (rc) return rc;
@@ -1432,12 +1446,12 @@ extern "C" int snn_autotune_batch(const snn_handle *hs, int32_t n, uint32_t tria
   int status = trial(orig, 2, &orig_ms);
   for (int fb : {128, 256, 512})
     for (int ips : {2, 4, 8, 16})
-      for (int ch : {64, 128, 192, 256}) {
+      for (int ln : {8, 16, 32}) {
         if (status != SNN_OK) break;
         snn_launch c = orig;
         c.fused_block = fb;
         c.fused_items_per_sm = ips;
-        c.deliver_chunk = ch;
+        c.deliver_lanes = ln;
         float ms = 0;
         status = trial(c, 1, &ms);
         if (status == SNN_OK && ms < best_ms) {
@@ -1472,26 +1486,18 @@ extern "C" int snn_set_launch(snn_handle h, const snn_launch *cfg) {
     return fail(SNN_ERR_ARG, "fused_block must be a multiple of 32 in 128..512");
   if (c.fused_items_per_sm < 1 || c.fused_items_per_sm > 32) return fail(SNN_ERR_ARG, "fused_items_per_sm in 1..32");
   if (c.window_steps < 1 || c.window_steps > 4096) return fail(SNN_ERR_ARG, "window_steps in 1..4096");
-  if (c.deliver_chunk < 8 || c.deliver_chunk % 8 || (uint32_t)c.deliver_chunk > max_chunk_records())
-    return fail(SNN_ERR_ARG, "deliver_chunk must be a multiple of 8 in 8..1152");
+  if (c.deliver_lanes != 4 && c.deliver_lanes != 8 && c.deliver_lanes != 16 && c.deliver_lanes != 32)
+    return fail(SNN_ERR_ARG, "deliver_lanes must be 4, 8, 16 or 32");
   if (c.update_groups != 1 && c.update_groups != 2 && c.update_groups != 4)
     return fail(SNN_ERR_ARG, "update_groups must be 1, 2 or 4");
   if (c.update_block == 512 && c.update_groups == 4)
     return fail(SNN_ERR_ARG, "update_groups 4 needs update_block <= 256");
   if (c.l2_persist != 0 && c.l2_persist != 1) return fail(SNN_ERR_ARG, "l2_persist must be 0 or 1");
   if (c.deliver_blocks < 1 || c.deliver_blocks > 32) return fail(SNN_ERR_ARG, "deliver_blocks must be in 1..32");
-  if ((size_t)c.deliver_warps * 2u * (size_t)c.deliver_chunk * 8u > 200u * 1024u)
-    return fail(SNN_ERR_ARG, "deliver_warps x deliver_chunk records exceed the staging limit (200 KB per block)");
   h->cfg = c;
   return SNN_OK;
 }
 
-extern "C" int snn_debug_set_wait_limit(snn_handle h, uint32_t iterations) {
-  if (!h) return fail(SNN_ERR_ARG, "null handle");
-  h->wait_limit = iterations;
-  h->hd.wait_limit = iterations;
-  return SNN_OK;
-}
 
 // ---------------------------------------------------------------------------
 // autotuner: time candidate shapes from a snapshot of the state, restore the
@@ -1535,12 +1541,12 @@ extern "C" int snn_autotune(snn_handle h, uint32_t trial_steps) {
     }
   for (int fb : {128, 256})
     for (int ips : {4, 8, 16})
-      for (int ch : {256, 128}) {
+      for (int ln : {8, 16}) {
         snn_launch c = orig;
         c.path = 1;
         c.fused_block = fb;
         c.fused_items_per_sm = ips;
-        c.deliver_chunk = ch;
+        c.deliver_lanes = ln;
         cands.push_back(c);
       }
   cudaEvent_t e0, e1;
@@ -1586,18 +1592,19 @@ extern "C" int snn_autotune(snn_handle h, uint32_t trial_steps) {
   status = trial(orig, 3, &orig_ms);
   if (status == SNN_OK) run_cands();
   if (status == SNN_OK && best.path == 0) {
-    // stage 2: delivery shapes with the best update shape.  Fewer than 8
-    // blocks per SM time well alone but, with small staging buffers, slowed
-    // two networks running concurrently by 11%: they are not tried.
+    // stage 2: delivery shapes with the best update shape (blocks per SM
+    // matter only when the grid has more modules than the delivery grid)
     cands.clear();
-    for (int dw : {2, 4})
-      for (int ch : {1152, 576, 384, 192})
-        for (int db : {8, 16}) {
+    const int sms = h->sm_count > 0 ? h->sm_count : 148;
+    const bool many_modules = (int64_t)L.G > (int64_t)sms * 4;
+    for (int dw : {2, 4, 8})
+      for (int ln : {4, 8, 16, 32})
+        for (int db : {4, 8, 16}) {
+          if (!many_modules && db != best.deliver_blocks) continue;
           snn_launch c = best;
           c.deliver_warps = dw;
-          c.deliver_chunk = ch;
+          c.deliver_lanes = ln;
           c.deliver_blocks = db;
-          if ((size_t)dw * 2u * (size_t)ch * 8u * (size_t)db > 224u * 1024u) continue;   // resident blocks only
           cands.push_back(c);
         }
     run_cands();

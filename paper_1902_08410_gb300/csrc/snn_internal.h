@@ -16,7 +16,6 @@ constexpr int kMaxM = 4096;       // out-degree limit
 constexpr int kNeuronAlign = 128; // neuron arrays padded to a multiple of 128
 
 // status bits written by kernels
-constexpr uint32_t kStatusTimeout = 1u;
 constexpr uint32_t kStatusRasterOverflow = 2u;
 
 // Time window of one graph replay (device memory, rewritten by the host
@@ -32,7 +31,7 @@ struct alignas(16) NetWin {
 struct alignas(16) RecHeader {
   uint32_t cursor;        // raster entries appended in this window
   uint32_t status;        // kStatus* bits
-  uint32_t step_base[2];  // first entry of the step with that parity
+  uint32_t pad[2];
 };
 
 // Static description of a network.  Passed by value as a kernel parameter on
@@ -44,7 +43,7 @@ struct alignas(16) NetDev {
   uint32_t G, gx;       // modules, grid width
   uint32_t M;           // out-degree
   uint32_t M_pad;       // padded to a multiple of 8
-  uint32_t D;           // ring slots = n_delay + 1
+  uint32_t D;           // history slots = n_delay + 1
   uint32_t fmt;         // 0 = f32 weights, 1 = i16 weights
   uint32_t row_bytes;   // bytes of one row: M_pad keys then M_pad weights
   uint32_t bin_steps;
@@ -52,7 +51,9 @@ struct alignas(16) NetDev {
   uint32_t slot;        // index of this network in a batch
   uint32_t rec_cap;     // raster entries per window
   uint32_t rates_bins;  // bins in the rate window
-  uint32_t wait_limit;  // bounded-wait iterations
+  uint32_t n_delay;     // largest delay in steps (D - 1)
+  uint32_t os;          // u16 entries per row of the delay-group table (multiple of 8)
+  uint32_t pad1[3];
 
   // --- per population constants (Eq. 2 propagators, Table S1)
   float pvv[kNPop], pvc[kNPop], pcc[kNPop];
@@ -65,8 +66,17 @@ struct alignas(16) NetDev {
   float *V;             // [N_pad]
   float *c;             // [N_pad]
   uint8_t *ref;         // [N_pad]
-  int32_t *ring;        // [D][N_pad], 2^-16 mV
+  // Synaptic input of step t (2^-16 mV) = acc_loc[t & 1][n] + acc_rem[t & 1][n].
+  // acc_loc holds what neurons receive from sources of their own module; the
+  // delivery writes it with plain stores (every entry, every step).  acc_rem
+  // receives reductions from other modules' sources (and, on the fused path,
+  // the delay-1 records of the step's own spikes); the update clears it.
+  int32_t *acc_loc;     // [2][N_pad]
+  int32_t *acc_rem;     // [2][N_pad]
+  uint32_t *hcnt;       // [D][G] spikes of module m at a step with slot t mod D
+  uint32_t *hist;       // [D][N] their ids: slot s, module m at s * N + m * 1250
   uint8_t *rows;        // [N][row_bytes]
+  const uint16_t *offs; // [N][os] delay groups: records with delay <= d end at offs[s * os + d]
   const int32_t *amp;   // [3][kZTab] external amplitudes, 2^-16 mV
   const NetWin *win;    // current window
   RecHeader *rec;       // recording header
@@ -85,17 +95,20 @@ struct BuildDev {
   int32_t p_local_mode; // 1 when p_local >= 0 (local bucket shortcut valid), 0 otherwise
 };
 
-// Work item of the fused step kernel: a range of one network's neurons.
+// Work item of the fused step kernel: a range of one network's neurons to
+// update, and a range of its modules whose delayed input (delays >= 2) to deliver.
 struct FusedItem {
   uint32_t net;         // index into the NetDev table
   uint32_t n_begin;     // first neuron (multiple of 4)
+  uint32_t m_begin;     // first module delivered
+  uint32_t m_end;       // one past the last module delivered
 };
 
 struct FusedTable {
   const NetDev *nets;
   const FusedItem *items;
   const uint32_t *n_items;  // item count in device memory (the graph outlives any one batch)
-  uint32_t chunk;           // records per delivery chunk
+  uint32_t lanes;           // lanes per delivery segment
 };
 
 // ---- launchers (snn_kernels.cu) -------------------------------------------
@@ -109,12 +122,12 @@ struct L2Window {
   float hit_ratio = 0.0f;
 };
 cudaError_t launch_update(const NetDev &nd, uint32_t k, int block, int groups, const L2Window &l2, cudaStream_t s);
-cudaError_t launch_deliver(const NetDev &nd, uint32_t k, uint32_t chunk, int warps, int blocks, const L2Window &l2,
+cudaError_t launch_deliver(const NetDev &nd, uint32_t k, uint32_t lanes, int warps, int blocks, const L2Window &l2,
                            cudaStream_t s);
 cudaError_t launch_fused(const FusedTable &tab, uint32_t k, int block, int blocks, cudaStream_t s);
-uint32_t max_chunk_records();        // largest chunk of the two-kernel delivery
-uint32_t max_fused_chunk_records();  // largest chunk of the fused step
 int fused_blocks_per_sm(int block);   // resident fused blocks per SM
+// u16 entries per row of the delay-group table
+inline uint32_t offs_stride(uint32_t n_delay) { return (n_delay + 1u + 7u) & ~7u; }
 int device_sm_count();
 
 }  // namespace snn

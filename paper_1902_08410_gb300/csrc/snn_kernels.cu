@@ -3,8 +3,8 @@
 // Arithmetic contract (identical on every path, no FMA contraction: the
 // dynamics use explicit __fmul_rn/__fadd_rn and the file is built with
 // -fmad=false):
-//   Eq. 2 over one step for neuron n at step t (slot st = t mod D):
-//     I  = ring[st][n]; ring[st][n] = 0
+//   Eq. 2 over one step for neuron n at step t:
+//     I  = synaptic input of step t (int32, 2^-16 mV), cleared once read
 //     w  = word (n mod 4) of Philox4x32-10(key = seed, ctr = (n div 4, t, 1, 0))
 //     k  = #{j < 16 : (w >> 12) >= thr[pop][j]}     (Poisson count, Sec. 2.1)
 //     I += amp[pop][z_e] for the k external events: z_0 = w & 0xFFF, z_e (e >= 1)
@@ -12,9 +12,21 @@
 //     ref > 0 : ref -= 1, V = V_r                    (refractory clamp, Sec. 2.2)
 //     else    : V = (E + (P_VV*(V-E) + P_Vc*c)) + I*2^-16; spike if V > V_th
 //     c = P_cc*c (+ alpha when the neuron fired)
-//   Delivery of a spike of step t: every record (d, target, w) of the source's
-//   row adds its fixed-point weight to ring[(t+d) mod D][target] (int32
+//   Delivery (Sec. 2.1.1): a spike of source s at step t reaches the target of
+//   each record (d, target, w) of s's row at step t + d: the record's
+//   fixed-point weight is added to the target's input of step t + d (int32
 //   reductions, so the sum does not depend on order).
+//
+// Delay-major delivery.  A row is stored grouped by delay (Sec. 2.1), with the
+// end of each delay group in a small table (offs).  At step t the delivery
+// adds, for d = 1..n_delay, the delay-d group of every spike of step
+// t + 1 - d, so every record handled at step t lands in the input of step
+// t + 1: the input is two int32 buffers per neuron (parity of t) instead of a
+// ring of n_delay + 1 slots.  The spikes of the last n_delay steps are kept
+// per (step slot, module) in `hist`.  A delivery block owns one module m at a
+// time: records of m's spikes whose target lies in m (80-100% of them) are
+// summed in shared memory and stored once per neuron (acc_loc); the others
+// are reduced into acc_rem.
 #include <algorithm>
 #include <cstdint>
 
@@ -49,62 +61,20 @@ __device__ __forceinline__ int pop_of_local(uint32_t local) { return local < 250
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// ---------------------------------------------------------------------------
-// Asynchronous bulk copies (TMA, non-tensor) into shared memory with mbarriers.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
 // Fire-and-forget prefetch of [src, src + bytes) into L2 (16-byte aligned
 // address, size a multiple of 16).
 __device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ uint64_t l2_evict_first_policy() {
-  uint64_t pol;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-  return pol;
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar,
-                                         uint64_t pol) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
-          "r"(dst),
-      "l"(src), "r"(bytes), "r"(bar), "l"(pol)
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait: at most `limit` polls (each poll may suspend briefly).
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint32_t limit) {
-  for (uint32_t i = 0; i < limit; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
 
-constexpr uint32_t kDefaultWaitLimit = 1u << 22;
+// Prefetch the byte range [p, p + bytes) widened to 16-byte boundaries; the
+// caller guarantees the widened range lies inside one allocation.
+__device__ __forceinline__ void prefetch_range_l2(const uint8_t *p, uint32_t bytes) {
+  if (bytes == 0) return;
+  const uintptr_t a0 = reinterpret_cast<uintptr_t>(p) & ~uintptr_t(15);
+  const uintptr_t a1 = (reinterpret_cast<uintptr_t>(p) + bytes + 15u) & ~uintptr_t(15);
+  bulk_prefetch_l2(reinterpret_cast<const void *>(a0), (uint32_t)(a1 - a0));
+}
 
 // Programmatic dependent launch: wait for the previous kernel in the stream
 // (no-op when launched without the attribute), then let the next one launch.
@@ -119,6 +89,9 @@ __device__ __forceinline__ void red_add_s32(int32_t *addr, int32_t v) {
 }
 __device__ __forceinline__ void red_add_u32(uint32_t *addr, uint32_t v) {
   asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_u64(unsigned long long *addr, unsigned long long v) {
+  asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(addr), "l"(v) : "memory");
 }
 
 // Loads that bypass L1 (streamed state), keeping L1 for the amplitude table.
@@ -140,6 +113,22 @@ __device__ __forceinline__ uint32_t ld_na_u32(const uint32_t *p) {
   uint32_t v;
   asm volatile("ld.global.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
   return v;
+}
+// Read-only loads of synapse records, not kept in L1 (each is used once).
+__device__ __forceinline__ uint32_t ld_rec_u32(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float ld_rec_f32(const float *p) {
+  float v;
+  asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ int32_t ld_rec_s16(const int16_t *p) {
+  int16_t v;
+  asm volatile("ld.global.nc.L1::no_allocate.s16 %0, [%1];" : "=h"(v) : "l"(p));
+  return (int32_t)v;
 }
 
 // ---------------------------------------------------------------------------
@@ -229,9 +218,6 @@ __device__ __forceinline__ void extra_events_warp(const NetDev &nd, uint32_t n0,
   }
 }
 
-__device__ __forceinline__ void red_add_u64(unsigned long long *addr, unsigned long long v) {
-  asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(addr), "l"(v) : "memory");
-}
 
 __device__ __forceinline__ bool neuron_step(const NetDev &nd, int pop, float &V, float &c, uint32_t &ref, int32_t I) {
   bool spike = false;
@@ -265,7 +251,7 @@ __device__ __forceinline__ bool neuron_step(const NetDev &nd, int pop, float &V,
 struct Group4 {
   float4 V, c;
   uint32_t ref;   // 4 x u8
-  int4 I;         // ring slot t
+  int4 Il, Ir;    // input of the step from the module's own sources / from the others
 };
 
 __device__ __forceinline__ void load_state4(const NetDev &nd, uint32_t n0, Group4 &g) {
@@ -275,17 +261,19 @@ __device__ __forceinline__ void load_state4(const NetDev &nd, uint32_t n0, Group
   g.ref = ld_na_u32(reinterpret_cast<const uint32_t *>(nd.ref) + i4);
 }
 
-// The slot is cleared by step4 after the neuron state is stored: a store right
-// behind the load to the same address held every later load of the warp back
-// (the whole step took ~1.7x longer on a 720k-neuron grid).
-__device__ __forceinline__ void load_ring4(const NetDev &nd, uint32_t n0, uint32_t st, Group4 &g) {
-  g.I = ld_na_i4(reinterpret_cast<const int4 *>(nd.ring + (size_t)st * nd.N_pad) + (n0 >> 2));
+// Input buffers of the step with parity `par`.  The remote buffer is cleared by
+// step4 after the neuron state is stored: a store right behind the load to the
+// same address held every later load of the warp back.
+__device__ __forceinline__ void load_input4(const NetDev &nd, uint32_t n0, uint32_t par, Group4 &g) {
+  const size_t o = (size_t)par * nd.N_pad;
+  g.Il = ld_na_i4(reinterpret_cast<const int4 *>(nd.acc_loc + o) + (n0 >> 2));
+  g.Ir = ld_na_i4(reinterpret_cast<const int4 *>(nd.acc_rem + o) + (n0 >> 2));
 }
 
-// Advance the 4 neurons of g by step t (ring slot st, read by load_ring4 and
-// cleared here); returns the 4-bit spike mask and adds the number of external
+// Advance the 4 neurons of g by step t (input buffers of parity par, read by
+// load_input4); returns the 4-bit spike mask and adds the number of external
 // events to n_ext.
-__device__ __forceinline__ uint32_t step4(const NetDev &nd, uint32_t n0, uint32_t t, uint32_t st, Group4 &g,
+__device__ __forceinline__ uint32_t step4(const NetDev &nd, uint32_t n0, uint32_t t, uint32_t par, Group4 &g,
                                           uint32_t &n_ext) {
   // one counter-based draw serves the four neurons (word n mod 4 each)
   const uint4 R = philox4x32_10(n0 >> 2, t, 1u, 0u, nd.key0, nd.key1);
@@ -299,7 +287,8 @@ __device__ __forceinline__ uint32_t step4(const NetDev &nd, uint32_t n0, uint32_
     kx[q] = poisson_count(nd, pops[q], Wv[q]);
     local = (local + 1u == (uint32_t)kK) ? 0u : local + 1u;
   }
-  int32_t Iv[4] = {g.I.x, g.I.y, g.I.z, g.I.w};
+  // int32 sums: the order of the terms does not change the result
+  int32_t Iv[4] = {g.Il.x + g.Ir.x, g.Il.y + g.Ir.y, g.Il.z + g.Ir.z, g.Il.w + g.Ir.w};
 #pragma unroll
   for (int q = 0; q < 4; ++q)   // first external event: independent table loads
     if (kx[q]) Iv[q] += __ldg(nd.amp + pops[q] * kZTab + (Wv[q] & 0xFFFu));
@@ -320,7 +309,7 @@ __device__ __forceinline__ uint32_t step4(const NetDev &nd, uint32_t n0, uint32_
     reinterpret_cast<float4 *>(nd.V)[i4] = make_float4(Vv[0], Vv[1], Vv[2], Vv[3]);
     reinterpret_cast<float4 *>(nd.c)[i4] = make_float4(cv[0], cv[1], cv[2], cv[3]);
     reinterpret_cast<uint32_t *>(nd.ref)[i4] = rv[0] | (rv[1] << 8) | (rv[2] << 16) | (rv[3] << 24);
-    reinterpret_cast<int4 *>(nd.ring + (size_t)st * nd.N_pad)[i4] = make_int4(0, 0, 0, 0);
+    reinterpret_cast<int4 *>(nd.acc_rem + (size_t)par * nd.N_pad)[i4] = make_int4(0, 0, 0, 0);
   }
   return mask;
 }
@@ -328,33 +317,39 @@ __device__ __forceinline__ uint32_t step4(const NetDev &nd, uint32_t n0, uint32_
 __device__ __forceinline__ uint32_t update4(const NetDev &nd, uint32_t n0, uint32_t t, uint32_t &n_ext) {
   Group4 g;
   load_state4(nd, n0, g);
-  const uint32_t st = t % nd.D;
-  load_ring4(nd, n0, st, g);
-  return step4(nd, n0, t, st, g, n_ext);
+  const uint32_t par = t & 1u;
+  load_input4(nd, n0, par, g);
+  return step4(nd, n0, t, par, g, n_ext);
 }
 
 // Warp-level recording of the warp's spikes over G groups (all 32 lanes
 // active; in group g lane L owns neurons n0[g]..n0[g]+3, and the warp's 32
 // lanes cover one aligned 128-neuron tile).  Appends raster entries with one
-// returning atomic per warp, counts rates with fire-and-forget reductions and
-// adds each tile's external events to that tile's slot.  When `smem_list` is
-// given the ids are also appended there (block-local list for fused delivery).
+// returning atomic per warp, adds each spike to the step's history of its
+// module (one returning atomic per module the tile touches: a 128-neuron tile
+// lies in at most two 1250-neuron modules), counts rates with fire-and-forget
+// reductions, adds each tile's external events to that tile's slot and
+// prefetches into L2 the delay-group table and the first records of every
+// spiking neuron's row.  When `smem_list` is given the ids are also appended
+// there (block-local list for the fused step).
 template <int G>
 __device__ __forceinline__ void record_warp(const NetDev &nd, const uint32_t (&mask)[G], const uint32_t (&n0)[G],
                                             const uint32_t (&n_ext)[G], uint32_t t, uint32_t k, uint32_t bin0,
                                             uint32_t *smem_list, uint32_t *smem_count) {
   const uint32_t lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
-  uint32_t before[G], wtot = 0;
+  uint32_t below[G], gcnt[G], wtot = 0;
 #pragma unroll
   for (int g = 0; g < G; ++g) {
-    before[g] = wtot;
+    below[g] = 0;
+    gcnt[g] = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const uint32_t b = __ballot_sync(0xFFFFFFFFu, (mask[g] >> q) & 1u);
-      before[g] += __popc(b & lt);
-      wtot += __popc(b);
+      below[g] += __popc(b & lt);
+      gcnt[g] += __popc(b);
     }
+    wtot += gcnt[g];
     uint32_t ext = n_ext[g];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ext += __shfl_xor_sync(0xFFFFFFFFu, ext, o);
@@ -362,153 +357,231 @@ __device__ __forceinline__ void record_warp(const NetDev &nd, const uint32_t (&m
     if (lane == 0 && ext) red_add_u64(nd.ext_acc + tile, ext);   // slot owned by this warp
   }
   if (wtot == 0) return;
-  uint32_t gbase = 0, sbase = 0;
+  const uint32_t slot = t % nd.D;
+  // spikes of each group in the tile's first module (ids below the boundary
+  // come first in the lane-major, neuron-minor order used for ranks)
+  uint32_t ma[G], nlo[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    ma[g] = __shfl_sync(0xFFFFFFFFu, n0[g], 0) / (uint32_t)kK;
+    const uint32_t bnd = (ma[g] + 1u) * (uint32_t)kK;
+    uint32_t mine = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) mine += ((mask[g] >> q) & 1u) && (n0[g] + q < bnd) ? 1u : 0u;
+    nlo[g] = __reduce_add_sync(0xFFFFFFFFu, mine);
+  }
+  uint32_t gbase = 0, sbase = 0, hlo[G], hhi[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) hlo[g] = hhi[g] = 0;
   if (lane == 0) {
     gbase = atomicAdd(&nd.rec->cursor, wtot);
     if (smem_list) sbase = atomicAdd(smem_count, wtot);
+    uint32_t *hc = nd.hcnt + (size_t)slot * nd.G;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      if (nlo[g]) hlo[g] = atomicAdd(hc + ma[g], nlo[g]);
+      if (gcnt[g] > nlo[g]) hhi[g] = atomicAdd(hc + ma[g] + 1u, gcnt[g] - nlo[g]);
+    }
   }
   gbase = __shfl_sync(0xFFFFFFFFu, gbase, 0);
   sbase = __shfl_sync(0xFFFFFFFFu, sbase, 0);
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    hlo[g] = __shfl_sync(0xFFFFFFFFu, hlo[g], 0);
+    hhi[g] = __shfl_sync(0xFFFFFFFFu, hhi[g], 0);
+  }
   if (lane == 0 && gbase + wtot > nd.rec_cap) atomicOr(&nd.rec->status, kStatusRasterOverflow);
   const unsigned long long tag = ((unsigned long long)nd.slot << 48) | ((unsigned long long)k << 32);
   const uint32_t bin = t / nd.bin_steps - bin0;
+  const uint32_t wb = nd.fmt ? 2u : 4u;
+  const uint32_t pre_keys = min(512u, nd.M_pad * 4u), pre_w = min(512u, nd.M_pad * wb);
+  uint32_t goff = 0;
 #pragma unroll
   for (int g = 0; g < G; ++g) {
-    uint32_t pos = before[g];
+    uint32_t r = below[g];   // rank of the lane's next spike within group g
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if ((mask[g] >> q) & 1u) {
         const uint32_t id = n0[g] + q;
-        // the delivery reads this row next: start fetching it into L2 now
-        bulk_prefetch_l2(nd.rows + (size_t)id * nd.row_bytes, nd.row_bytes);
+        // the delivery reads this row's delay groups over the next steps
+        const uint8_t *row = nd.rows + (size_t)id * nd.row_bytes;
+        bulk_prefetch_l2(nd.offs + (size_t)id * nd.os, nd.os * 2u);
+        bulk_prefetch_l2(row, pre_keys);
+        bulk_prefetch_l2(row + (size_t)nd.M_pad * 4u, pre_w);
+        const uint32_t pos = goff + r;
         if (gbase + pos < nd.rec_cap) nd.rec_entries[gbase + pos] = tag | id;
         if (smem_list) smem_list[sbase + pos] = id;
         const uint32_t m = id / (uint32_t)kK;
+        const uint32_t hpos = (m == ma[g]) ? hlo[g] + r : hhi[g] + (r - nlo[g]);
+        nd.hist[(size_t)slot * nd.N + (size_t)m * kK + hpos] = id;
         red_add_u32(nd.rates + ((size_t)bin * nd.G + m) * 3u + pop_of_local(id - m * (uint32_t)kK), 1u);
-        ++pos;
+        ++r;
       }
     }
+    goff += gcnt[g];
   }
 }
 
 // ---------------------------------------------------------------------------
-// Delivery: warps take work items (spike, chunk of its row); the chunk's keys
-// and weights are staged in shared memory by bulk asynchronous copies (TMA),
-// double buffered with one mbarrier per buffer, then scattered into the ring
-// with fire-and-forget int32 reductions.
+// Delay-major delivery of one module (Sec. 2.1.1): for d = d_first..n_delay,
+// the delay-d records of the module's spikes of step t + 1 - d, all of which
+// land in the input of step t + 1.
 // ---------------------------------------------------------------------------
-struct WarpStage {
-  uint8_t *buf0, *buf1;  // chunk buffers: keys, then weights
-  uint32_t bar0, bar1;   // mbarrier shared addresses
-  uint32_t ph0, ph1;     // phase parity per buffer
-  uint32_t cap;          // records the buffers hold
+constexpr uint32_t kSegCap = 512;   // (spike, delay) segments described per pass
+
+struct alignas(16) DeliverShared {
+  int32_t acc[kK + 2];        // input of the module's neurons from its own sources
+  uint32_t pre[260];          // pre[d]: segments with delay <= d (pre[0] = 0)
+  uint32_t src[kSegCap];      // source neuron of each segment of the pass
+  uint32_t rng[kSegCap];      // its records [lo, hi): lo | hi << 16
 };
 
-__device__ __forceinline__ void init_stage(WarpStage &ws, uint8_t *base, uint64_t *bars, uint32_t cap) {
-  ws.buf0 = base;
-  ws.buf1 = base + (size_t)cap * 8u;
-  ws.bar0 = smem_u32(bars);
-  ws.bar1 = smem_u32(bars + 1);
-  ws.ph0 = ws.ph1 = 0u;
-  ws.cap = cap;
-  if (lane_id() == 0) {
-    mbar_init(ws.bar0, 1);
-    mbar_init(ws.bar1, 1);
-    fence_mbar_init();
-    fence_proxy_async_smem();
-  }
-  __syncwarp();
+__device__ __forceinline__ uint32_t slot_back(uint32_t tm, uint32_t d, uint32_t D) {
+  return (tm + 1u + D - d) % D;   // slot of step t + 1 - d, tm = t mod D, 1 <= d < D
 }
 
-// Issue the copy of records [j0, j0 + n) of row `src` into buffer b (leader lane).
-__device__ __forceinline__ void issue_chunk(const NetDev &nd, uint8_t *buf, uint32_t bar, uint32_t chunk,
-                                            uint32_t src, uint32_t j0, uint64_t pol) {
-  const uint32_t n = min(chunk, nd.M_pad - j0);
+// Add the records [a, b) of source s's row: targets inside the module
+// [mbase, mbase + 1250) into shared memory, the others into `rem`.
+__device__ __forceinline__ void add_records(const NetDev &nd, DeliverShared &sh, int32_t *rem, uint32_t s,
+                                            uint32_t a, uint32_t b, uint32_t sub, uint32_t lanes, uint32_t mbase) {
+  const uint8_t *row = nd.rows + (size_t)s * nd.row_bytes;
+  const uint32_t *keys = reinterpret_cast<const uint32_t *>(row);
+  const uint8_t *wrow = row + (size_t)nd.M_pad * 4u;
+  for (uint32_t r = a + sub; r < b; r += 4u * lanes) {
+    uint32_t kk[4];
+    int32_t vv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {   // the loads first, then the additions
+      const uint32_t rr = r + (uint32_t)u * lanes;
+      kk[u] = 0xFFFFFFFFu;
+      vv[u] = 0;
+      if (rr < b) {
+        kk[u] = ld_rec_u32(keys + rr);
+        vv[u] = nd.fmt ? ld_rec_s16(reinterpret_cast<const int16_t *>(wrow) + rr) * 64
+                       : __float2int_rn(__fmul_rn(ld_rec_f32(reinterpret_cast<const float *>(wrow) + rr), 65536.0f));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (r + (uint32_t)u * lanes < b) {
+        const uint32_t tgt = kk[u] & 0xFFFFFFu;
+        const uint32_t lt = tgt - mbase;
+        if (lt < (uint32_t)kK) atomicAdd(&sh.acc[lt], vv[u]);
+        else red_add_s32(rem + tgt, vv[u]);
+      }
+    }
+  }
+}
+
+// Block-wide (every thread calls it with the same arguments).  sh.acc is zero
+// on entry and on return.
+__device__ __forceinline__ void deliver_module(const NetDev &nd, DeliverShared &sh, uint32_t t, uint32_t m, uint32_t d_first,
+                               uint32_t lanes) {
+  const uint32_t tid = threadIdx.x, nthr = blockDim.x;
+  const uint32_t D = nd.D, nd_max = nd.n_delay, tm = t % D;
+  const uint32_t par1 = (t + 1u) & 1u;
+  const uint32_t mbase = m * (uint32_t)kK;
+  // 1. segments per delay and their prefix sums (one warp; n_delay <= 254)
+  if (tid < 32u) {
+    uint32_t v[8], sum = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const uint32_t d = tid * 8u + 1u + (uint32_t)i;
+      v[i] = (d >= d_first && d <= nd_max) ? nd.hcnt[(size_t)slot_back(tm, d, D) * nd.G + m] : 0u;
+      sum += v[i];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (tid >= (uint32_t)o) incl += y;
+    }
+    uint32_t acc = incl - sum;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      acc += v[i];
+      sh.pre[tid * 8u + 1u + (uint32_t)i] = acc;
+    }
+    if (tid == 0) sh.pre[0] = 0u;
+  }
+  __syncthreads();
+  const uint32_t S = sh.pre[nd_max];
+  int32_t *rem = nd.acc_rem + (size_t)par1 * nd.N_pad;
+  const uint32_t grp = tid / lanes, sub = tid % lanes, ngrp = nthr / lanes;
   const uint32_t wb = nd.fmt ? 2u : 4u;
-  const uint8_t *row = nd.rows + (size_t)src * nd.row_bytes;
-  const uint32_t kbytes = n * 4u, wbytes = n * wb;
-  mbar_expect_tx(bar, kbytes + wbytes);
-  bulk_g2s(smem_u32(buf), row + (size_t)j0 * 4u, kbytes, bar, pol);
-  bulk_g2s(smem_u32(buf + (size_t)chunk * 4u), row + (size_t)nd.M_pad * 4u + (size_t)j0 * wb, wbytes, bar, pol);
+  for (uint32_t p0 = 0; p0 < S; p0 += kSegCap) {
+    const uint32_t np = min(kSegCap, S - p0);
+    // 2. describe the pass's segments: source, and its delay-d records
+    for (uint32_t j = tid; j < np; j += nthr) {
+      const uint32_t kseg = p0 + j;
+      uint32_t lo = 1u, hi = nd_max;   // smallest d with pre[d] > kseg
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (sh.pre[mid] > kseg) hi = mid; else lo = mid + 1u;
+      }
+      const uint32_t d = lo, i = kseg - sh.pre[d - 1u];
+      const uint32_t s = nd.hist[(size_t)slot_back(tm, d, D) * nd.N + mbase + i];
+      const uint16_t *o = nd.offs + (size_t)s * nd.os;
+      const uint32_t a = o[d - 1u], b = o[d];
+      sh.src[j] = s;
+      sh.rng[j] = a | (b << 16);
+      if (d < nd_max) {   // this spike's next delay group is read at the next step
+        const uint32_t c2 = o[d + 1u];
+        if (c2 > b) {
+          const uint8_t *row = nd.rows + (size_t)s * nd.row_bytes;
+          prefetch_range_l2(row + (size_t)b * 4u, (c2 - b) * 4u);
+          prefetch_range_l2(row + (size_t)nd.M_pad * 4u + (size_t)b * wb, (c2 - b) * wb);
+        }
+      }
+    }
+    __syncthreads();
+    // 3. their records, `lanes` lanes per segment
+    for (uint32_t j = grp; j < np; j += ngrp)
+      add_records(nd, sh, rem, sh.src[j], sh.rng[j] & 0xFFFFu, sh.rng[j] >> 16, sub, lanes, mbase);
+    __syncthreads();
+  }
+  // 4. the module's own input of step t + 1: one plain store per neuron
+  int2 *dst = reinterpret_cast<int2 *>(nd.acc_loc + (size_t)par1 * nd.N_pad + mbase);
+  int2 *src = reinterpret_cast<int2 *>(sh.acc);
+  for (uint32_t i = tid; i < (uint32_t)kK / 2u; i += nthr) {
+    dst[i] = src[i];
+    src[i] = make_int2(0, 0);
+  }
+  if (tid == 0) nd.hcnt[(size_t)((tm + 1u) % D) * nd.G + m] = 0u;   // the slot step t + 1 appends to
+  __syncthreads();
 }
 
-__device__ __forceinline__ void scatter_chunk(const NetDev &nd, const uint8_t *buf, uint32_t chunk, uint32_t j0,
-                                              uint32_t st) {
-  const uint32_t nvalid = j0 < nd.M ? min(chunk, nd.M - j0) : 0u;
-  const uint32_t *keys = reinterpret_cast<const uint32_t *>(buf);
-  const uint8_t *wbase = buf + (size_t)chunk * 4u;
-  int32_t *ring = nd.ring;
-  const uint32_t D = nd.D;
-  const size_t npad = nd.N_pad;
-  if (nd.fmt) {
-    const int16_t *wq = reinterpret_cast<const int16_t *>(wbase);
-    for (uint32_t i = lane_id(); i < nvalid; i += 32u) {
-      const uint32_t key = keys[i];
-      uint32_t slot = st + (key >> 24);
-      slot = slot >= D ? slot - D : slot;
-      red_add_s32(ring + (size_t)slot * npad + (key & 0xFFFFFFu), (int32_t)wq[i] * 64);
+// Fused step: the delay-1 records of the block's own spikes of step t,
+// reduced straight into the remote buffer of step t + 1 (the module's history
+// of step t is not complete while other blocks still update its neurons).
+__device__ void deliver_own_delay1(const NetDev &nd, const uint32_t *ids, uint32_t cnt, uint32_t t, uint32_t lanes) {
+  const uint32_t tid = threadIdx.x;
+  const uint32_t grp = tid / lanes, sub = tid % lanes, ngrp = blockDim.x / lanes;
+  int32_t *rem = nd.acc_rem + (size_t)((t + 1u) & 1u) * nd.N_pad;
+  const uint32_t wb = nd.fmt ? 2u : 4u;
+  for (uint32_t j = grp; j < cnt; j += ngrp) {
+    const uint32_t s = ids[j];
+    const uint16_t *o = nd.offs + (size_t)s * nd.os;
+    const uint32_t b = o[1];
+    const uint8_t *row = nd.rows + (size_t)s * nd.row_bytes;
+    const uint32_t *keys = reinterpret_cast<const uint32_t *>(row);
+    const uint8_t *wrow = row + (size_t)nd.M_pad * 4u;
+    if (sub == 0 && nd.n_delay > 1u) {
+      const uint32_t c2 = o[2];
+      if (c2 > b) {
+        prefetch_range_l2(row + (size_t)b * 4u, (c2 - b) * 4u);
+        prefetch_range_l2(wrow + (size_t)b * wb, (c2 - b) * wb);
+      }
     }
-  } else {
-    const float *wf = reinterpret_cast<const float *>(wbase);
-    for (uint32_t i = lane_id(); i < nvalid; i += 32u) {
-      const uint32_t key = keys[i];
-      uint32_t slot = st + (key >> 24);
-      slot = slot >= D ? slot - D : slot;
-      red_add_s32(ring + (size_t)slot * npad + (key & 0xFFFFFFu), __float2int_rn(__fmul_rn(wf[i], 65536.0f)));
+    for (uint32_t r = sub; r < b; r += lanes) {
+      const uint32_t key = ld_rec_u32(keys + r);
+      const int32_t v = nd.fmt ? ld_rec_s16(reinterpret_cast<const int16_t *>(wrow) + r) * 64
+                               : __float2int_rn(__fmul_rn(ld_rec_f32(reinterpret_cast<const float *>(wrow) + r),
+                                                          65536.0f));
+      red_add_s32(rem + (key & 0xFFFFFFu), v);
     }
   }
 }
-
-// Deliver work items first, first + stride, ... < n_items, where item i is
-// chunk (i % nch) of the row of source src_of(i / nch).  Returns false when a
-// bounded wait gave up (the status bit is set; copies in flight are drained).
-template <typename SrcOf>
-__device__ bool deliver_items(const NetDev &nd, WarpStage &ws, uint32_t chunk, uint32_t first, uint32_t stride,
-                              uint32_t n_items, uint32_t st, SrcOf src_of) {
-  if (first >= n_items) return true;
-  const uint32_t nch = (nd.M_pad + chunk - 1u) / chunk;
-  const uint64_t pol = l2_evict_first_policy();
-  const bool leader = lane_id() == 0;
-  if (leader) issue_chunk(nd, ws.buf0, ws.bar0, chunk, src_of(first / nch), (first % nch) * chunk, pol);
-  uint32_t b = 0;
-  for (uint32_t i = first; i < n_items; i += stride) {
-    const uint32_t nxt = i + stride;
-    if (nxt < n_items && leader) {
-      if (b == 0) issue_chunk(nd, ws.buf1, ws.bar1, chunk, src_of(nxt / nch), (nxt % nch) * chunk, pol);
-      else issue_chunk(nd, ws.buf0, ws.bar0, chunk, src_of(nxt / nch), (nxt % nch) * chunk, pol);
-    }
-    const uint32_t bar = b ? ws.bar1 : ws.bar0;
-    const uint32_t ph = b ? ws.ph1 : ws.ph0;
-    bool got = mbar_wait_bounded(bar, ph, nd.wait_limit);
-    got = __all_sync(0xFFFFFFFFu, got);
-    if (!got) {
-      // drain the copies in flight (each with the default limit), keeping the
-      // phases in step with the barriers; the caller stops using the stage
-      if (leader) atomicOr(&nd.rec->status, kStatusTimeout);
-      if (mbar_wait_bounded(bar, ph, kDefaultWaitLimit)) {
-        if (b) ws.ph1 ^= 1u; else ws.ph0 ^= 1u;
-      }
-      if (nxt < n_items && mbar_wait_bounded(b ? ws.bar0 : ws.bar1, b ? ws.ph0 : ws.ph1, kDefaultWaitLimit)) {
-        if (b) ws.ph0 ^= 1u; else ws.ph1 ^= 1u;
-      }
-      __syncwarp();
-      return false;
-    }
-    if (b) ws.ph1 ^= 1u; else ws.ph0 ^= 1u;
-    scatter_chunk(nd, b ? ws.buf1 : ws.buf0, chunk, (i % nch) * chunk, st);
-    __syncwarp();
-    fence_proxy_async_smem();   // our reads of this buffer precede its next async refill
-    __syncwarp();
-    b ^= 1u;
-  }
-  return true;
-}
-
-constexpr uint32_t kStageCap = 1152;   // records per staging buffer of k_deliver (f32: 9216 B)
-constexpr uint32_t kFusedCap = 256;    // records per staging buffer of k_fused
-
-uint32_t max_chunk_records() { return kStageCap; }
-uint32_t max_fused_chunk_records() { return kFusedCap; }
 
 // ---------------------------------------------------------------------------
 // Kernel: initial state (V uniform on [0, V_th) from Philox stream 2).
@@ -701,6 +774,23 @@ __global__ void __launch_bounds__(kBuildWarpsMax * 32) k_build_rows(const __grid
         ow[p] = w;
       }
     }
+    // 5. delay groups of the row: records with delay <= d end at offs[d]
+    //    (binary search of the sorted keys, one delay per lane)
+    if (nd.offs) {
+      uint16_t *orow = const_cast<uint16_t *>(nd.offs) + (size_t)s * nd.os;
+      for (uint32_t d = lane; d < nd.os; d += 32u) {
+        uint32_t lo = 0, hi = M;
+        if (d < nd_del) {
+          while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if ((w_key[w_perm[mid]] >> 24) <= d) lo = mid + 1u; else hi = mid;
+          }
+        } else {
+          lo = M;
+        }
+        orow[d] = (uint16_t)lo;
+      }
+    }
     __syncwarp();
   }
 }
@@ -712,7 +802,7 @@ __global__ void __launch_bounds__(kBuildWarpsMax * 32) k_build_rows(const __grid
 // Each thread advances G groups of 4 neurons; group g of block b covers the
 // neuron range ((b * G + g) * BLOCK + thread) * 4, so every warp owns whole
 // aligned 128-neuron tiles.  The state loads of all groups are issued before
-// the window is read, then the ring slots once the step is known.
+// the window is read, then the input buffers once the step is known.
 // One group per thread is capped at 48 registers (40 resident warps per SM), so
 // that a 720k-neuron grid (37 warps per SM) runs in a single wave.
 template <int BLOCK, int G>
@@ -736,16 +826,16 @@ __global__ void __launch_bounds__(BLOCK, G == 1 ? 1280 / BLOCK : 1) k_update(con
   const NetWin w = *nd.win;
   const uint32_t t = w.t0 + k;
   if (t >= w.t_end) return;
-  const uint32_t slot = t % nd.D;
+  const uint32_t par = t & 1u;
 #pragma unroll
   for (int g = 0; g < G; ++g)
-    if (live[g]) load_ring4(nd, n0[g], slot, st4[g]);
+    if (live[g]) load_input4(nd, n0[g], par, st4[g]);
   uint32_t mask[G], n_ext[G];
 #pragma unroll
   for (int g = 0; g < G; ++g) {
     mask[g] = 0;
     n_ext[g] = 0;
-    if (live[g]) mask[g] = step4(nd, n0[g], t, slot, st4[g], n_ext[g]);
+    if (live[g]) mask[g] = step4(nd, n0[g], t, par, st4[g], n_ext[g]);
   }
   // record per group whose tile is live (warp-uniform)
   if (live[G - 1]) {
@@ -762,65 +852,46 @@ __global__ void __launch_bounds__(BLOCK, G == 1 ? 1280 / BLOCK : 1) k_update(con
 }
 
 // ---------------------------------------------------------------------------
-// Kernel: spike delivery of step t (two-kernel path).  The step's spikes are
-// the raster entries [step_base, cursor) appended by k_update.
+// Kernel: delivery of step t (two-kernel path), every delay including 1 (the
+// update kernel of step t has completed its module histories).  Blocks take
+// modules m = blockIdx.x, blockIdx.x + gridDim.x, ...
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_deliver(const __grid_constant__ NetDev nd, uint32_t k, uint32_t chunk) {
-  extern __shared__ __align__(128) uint8_t smem[];
-  __shared__ uint64_t s_bars[16];
-  const RecHeader rh = *nd.rec;   // issued together with the window load
+__global__ void __launch_bounds__(256, 4) k_deliver(const __grid_constant__ NetDev nd, uint32_t k, uint32_t lanes) {
+  __shared__ DeliverShared sh;
   const NetWin w = *nd.win;
   const uint32_t t = w.t0 + k;
   if (t >= w.t_end) return;
-  const uint32_t cur = min(rh.cursor, nd.rec_cap);
-  const uint32_t base = rh.step_base[t & 1u];
-  if (blockIdx.x == 0 && threadIdx.x == 0) nd.rec->step_base[(t + 1u) & 1u] = cur;
-  const uint32_t count = cur > base ? cur - base : 0u;
-  const uint32_t nch = (nd.M_pad + chunk - 1u) / chunk;
-  const uint32_t n_items = count * nch;
-  const uint32_t warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const uint32_t gwarp = blockIdx.x * nw + warp, total = gridDim.x * nw;
-  if (gwarp >= n_items) return;
-  WarpStage ws;   // two staging buffers of `chunk` records per warp
-  init_stage(ws, smem + (size_t)warp * 2u * chunk * 8u, s_bars + 2 * warp, chunk);
-  const unsigned long long *ent = nd.rec_entries + base;
-  deliver_items(nd, ws, chunk, gwarp, total, n_items, t % nd.D,
-                [&](uint32_t s) { return (uint32_t)(ent[s] & 0xFFFFFFFFull); });
+  for (uint32_t i = threadIdx.x; i < (uint32_t)kK + 2u; i += blockDim.x) sh.acc[i] = 0;
+  __syncthreads();
+  for (uint32_t m = blockIdx.x; m < nd.G; m += gridDim.x) deliver_module(nd, sh, t, m, 1u, lanes);
 }
 
 // ---------------------------------------------------------------------------
 // Kernel: fused step over a table of networks.  A block takes work items
-// (network, 4*blockDim neurons): update, recording and a block-local spike
-// list, then its warps deliver those spikes.  Update reads ring slot t and
-// delivery writes slots t+1..t+D-1, so blocks need no grid-wide barrier; many
-// small blocks per SM let one block's update overlap another's delivery.
-// Launched with programmatic dependent launch: the prologue (barrier set-up,
-// descriptor copy, window read) runs while the previous step drains.
+// (network, 4*blockDim neurons, range of modules): update and recording with a
+// block-local spike list, the delay-1 records of those spikes, then the
+// delay >= 2 input of the item's modules.  Update reads the input buffers of
+// parity t and delivery writes those of parity t + 1, so blocks need no
+// grid-wide barrier; many small blocks per SM let one block's update overlap
+// another's delivery.  Launched with programmatic dependent launch: the
+// prologue (descriptor copy, window read) runs while the previous step drains.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(512) k_fused(const __grid_constant__ FusedTable tab, uint32_t k) {
-  extern __shared__ __align__(128) uint8_t smem[];
+  extern __shared__ __align__(128) uint8_t smem[];   // the item's spike ids (4 * blockDim)
   __shared__ NetDev nd;
   __shared__ NetWin s_win;
-  __shared__ uint64_t s_bars[32];
+  __shared__ DeliverShared sh;
   __shared__ uint32_t s_count;
   __shared__ uint32_t s_net;
-  __shared__ uint32_t s_abort;
-  const uint32_t npi = 4u * blockDim.x;
   uint32_t *s_ids = reinterpret_cast<uint32_t *>(smem);
-  uint8_t *stage_base = smem + (size_t)npi * 4u;
-  const uint32_t warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  WarpStage ws;
-  init_stage(ws, stage_base + (size_t)warp * 2u * kFusedCap * 8u, s_bars + 2 * warp, kFusedCap);
-  if (threadIdx.x == 0) {
-    s_net = 0xFFFFFFFFu;
-    s_abort = 0u;
-  }
+  const uint32_t warp = threadIdx.x >> 5;
+  for (uint32_t i = threadIdx.x; i < (uint32_t)kK + 2u; i += blockDim.x) sh.acc[i] = 0;
+  if (threadIdx.x == 0) s_net = 0xFFFFFFFFu;
   bool waited = false;
   const uint32_t n_items = *tab.n_items;
   for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
     const FusedItem item = tab.items[it];
     __syncthreads();   // the previous item is done with shared memory
-    if (s_abort) break;   // a bounded wait gave up: no further copies into the stages
     if (s_net != item.net) {
       const uint32_t *src = reinterpret_cast<const uint32_t *>(tab.nets + item.net);
       uint32_t *dst = reinterpret_cast<uint32_t *>(&nd);
@@ -846,12 +917,8 @@ __global__ void __launch_bounds__(512) k_fused(const __grid_constant__ FusedTabl
       record_warp<1>(nd, mask, a1, n_ext, t, k, s_win.bin0, s_ids, &s_count);
     }
     __syncthreads();
-    const uint32_t cnt = s_count;
-    if (cnt == 0) continue;
-    const uint32_t nch = (nd.M_pad + tab.chunk - 1u) / tab.chunk;
-    if (!deliver_items(nd, ws, tab.chunk, warp, nw, cnt * nch, t % nd.D, [&](uint32_t s) { return s_ids[s]; }) &&
-        lane_id() == 0)
-      s_abort = 1u;
+    deliver_own_delay1(nd, s_ids, s_count, t, tab.lanes);
+    for (uint32_t m = item.m_begin; m < item.m_end; ++m) deliver_module(nd, sh, t, m, 2u, tab.lanes);
   }
   if (!waited) {
     pdl_wait();
@@ -869,8 +936,8 @@ int device_sm_count() {
   return sms;
 }
 
-static size_t deliver_smem_bytes(int warps, uint32_t chunk) { return (size_t)warps * 2u * chunk * 8u; }
-static size_t fused_smem_bytes(int block) { return (size_t)block * 16u + (size_t)(block / 32) * 2u * kFusedCap * 8u; }
+static bool valid_lanes(uint32_t lanes) { return lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32; }
+static size_t fused_smem_bytes(int block) { return (size_t)block * 16u; }
 
 // Dynamic shared memory of one construction block: the device's opt-in
 // maximum per block (227 KB on sm_103), never above 227 KB.
@@ -887,11 +954,6 @@ static size_t build_smem_budget() {
 }
 
 cudaError_t prepare_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(k_deliver, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)deliver_smem_bytes(8, kStageCap));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem_bytes(512));
-  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_build_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)build_smem_budget());
 }
 
@@ -953,15 +1015,14 @@ cudaError_t launch_update(const NetDev &nd, uint32_t k, int block, int groups, c
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_deliver(const NetDev &nd, uint32_t k, uint32_t chunk, int warps, int blocks, const L2Window &l2,
+cudaError_t launch_deliver(const NetDev &nd, uint32_t k, uint32_t lanes, int warps, int blocks, const L2Window &l2,
                            cudaStream_t s) {
-  if (warps < 1 || warps > 8 || chunk < 8 || chunk > kStageCap || (chunk % 8)) return cudaErrorInvalidValue;
-  return launch_ex(k_deliver, dim3(blocks), dim3(warps * 32), deliver_smem_bytes(warps, chunk), l2, s, nd, k, chunk);
+  if (warps < 1 || warps > 8 || blocks < 1 || !valid_lanes(lanes)) return cudaErrorInvalidValue;
+  return launch_ex(k_deliver, dim3((unsigned)blocks), dim3(warps * 32), 0, l2, s, nd, k, lanes);
 }
 
 cudaError_t launch_fused(const FusedTable &tab, uint32_t k, int block, int blocks, cudaStream_t s) {
-  if (block < 128 || block > 512 || (block % 32)) return cudaErrorInvalidValue;
-  if (tab.chunk < 8 || tab.chunk > kFusedCap || (tab.chunk % 8)) return cudaErrorInvalidValue;
+  if (block < 128 || block > 512 || (block % 32) || !valid_lanes(tab.lanes)) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)blocks);
   cfg.blockDim = dim3((unsigned)block);

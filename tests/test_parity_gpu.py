@@ -241,19 +241,19 @@ def test_run_concurrent_matches_oracle(snn, oracle_mod):
 def test_launch_shapes_and_autotune_keep_results(snn, oracle_mod):
     p = W.base_params(3, 3, 0.4, "SWA")
     o = _oracle(oracle_mod, p, 21, 700)
-    shapes = [dict(path=0, update_block=128, update_groups=1, deliver_warps=2, window_steps=33, deliver_chunk=8),
-              dict(path=0, update_block=512, update_groups=2, deliver_warps=8, window_steps=700, deliver_chunk=1152),
-              dict(path=0, update_block=256, update_groups=4, deliver_warps=1, window_steps=50, deliver_chunk=200),
-              dict(path=0, update_block=128, update_groups=4, deliver_warps=4, window_steps=384, deliver_chunk=384),
-              dict(path=0, update_block=256, update_groups=1, deliver_warps=2, window_steps=128, deliver_chunk=384,
+    shapes = [dict(path=0, update_block=128, update_groups=1, deliver_warps=2, window_steps=33, deliver_lanes=4),
+              dict(path=0, update_block=512, update_groups=2, deliver_warps=8, window_steps=700, deliver_lanes=32),
+              dict(path=0, update_block=256, update_groups=4, deliver_warps=1, window_steps=50, deliver_lanes=16),
+              dict(path=0, update_block=128, update_groups=4, deliver_warps=4, window_steps=384, deliver_lanes=8),
+              dict(path=0, update_block=256, update_groups=1, deliver_warps=2, window_steps=128, deliver_lanes=32,
                    l2_persist=1),
-              dict(path=0, update_block=256, update_groups=1, deliver_warps=4, window_steps=90, deliver_chunk=192,
+              dict(path=0, update_block=256, update_groups=1, deliver_warps=4, window_steps=90, deliver_lanes=8,
                    deliver_blocks=16),
-              dict(path=0, update_block=128, update_groups=2, deliver_warps=8, window_steps=70, deliver_chunk=16,
+              dict(path=0, update_block=128, update_groups=2, deliver_warps=8, window_steps=70, deliver_lanes=4,
                    deliver_blocks=1, l2_persist=0),
-              dict(path=1, fused_block=128, fused_items_per_sm=1, window_steps=64, deliver_chunk=256),
-              dict(path=1, fused_block=512, fused_items_per_sm=4, window_steps=128, deliver_chunk=96),
-              dict(path=1, fused_block=128, fused_items_per_sm=16, window_steps=300, deliver_chunk=1152)]
+              dict(path=1, fused_block=128, fused_items_per_sm=1, window_steps=64, deliver_lanes=8),
+              dict(path=1, fused_block=512, fused_items_per_sm=4, window_steps=128, deliver_lanes=4),
+              dict(path=1, fused_block=128, fused_items_per_sm=16, window_steps=300, deliver_lanes=32)]
     for sh in shapes:
         g = snn.Network(p, 21)
         g.launch = sh
@@ -311,25 +311,6 @@ def test_l2_set_aside_restored(snn):
     assert limit() == raised          # b still holds the window
     b.close()
     assert limit() == before
-
-
-# ---------------------------------------------------------------------------
-# bounded waits: a wait that gives up is reported, the context stays usable
-# ---------------------------------------------------------------------------
-def test_wait_limit_zero_reports_timeout(snn):
-    p = W.base_params(2, 2, 1.0, "AW")
-    for path in (0, 1):
-        g = snn.Network(p, 4)
-        g.launch = {"path": path}
-        g.set_wait_limit(0)
-        with pytest.raises(snn.SnnError) as ei:
-            g.run(200)
-        assert ei.value.code == -4
-        g.close()
-    # the device is still healthy: a fresh network runs normally
-    g = snn.Network(p, 4)
-    g.run(50)
-    assert g.stats()["t"] == 50
 
 
 @pytest.mark.parametrize("fmt", [W.REC_F32, W.REC_I16])
