@@ -63,6 +63,8 @@ def parse_args():
                     help="run the two networks one after the other instead of concurrently")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="grid mode: skip the compact 64x64, 256-network batch and serving points")
     ap.add_argument("--mode", choices=["grid", "batch", "serve", "grid64", "profile", "table_s1"], default="grid",
                     help="grid: 24x24 SWA+AW (default); batch: 256-network SWA->AW sweep; serve: request "
                          "stream; grid64: 64x64 lambda sweep with f32 vs i16 records")
@@ -358,21 +360,61 @@ def run_gb300(args, dist: Dist):
         streams.append(torch.cuda.Stream())
         nets.append(snn.Network(wl["params"], wl["seed"] + 7919 * dist.rank, stream=streams[-1].cuda_stream))
         names.append(reg)
+    # Two ways to advance the pair: "concurrent" (two-kernel path, each network
+    # tuned alone, each on its own stream) and "batch" (both networks in one
+    # fused kernel per step, shape tuned on the pair).  After the initial
+    # volley both are tuned and timed on alternating stretches of the same run;
+    # the faster one is benchmarked.
+    form, form_trial = ("sequential" if args.sequential else "concurrent"), None
     if not args.no_tune:
         for n in nets:
             n.run(2000)
-            n.autotune(400)
+            n.autotune(400, path=0)
+        cfg_conc = [n.launch for n in nets]
+        cfg_batch = None
+        if not args.sequential:
+            cfg_batch = snn.autotune_batch(nets, 200)
+            form_trial = {"concurrent_ms": 0.0, "batch_ms": 0.0, "steps_each": 3 * 700}
+            for _ in range(3):
+                for f in ("concurrent", "batch"):
+                    for n, c in zip(nets, cfg_conc if f == "concurrent" else [cfg_batch] * len(nets)):
+                        n.launch = c
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    a.record(stream)
+                    for st in streams:
+                        st.wait_event(a)
+                    if f == "batch":
+                        snn.run_batch(nets, [700] * len(nets))
+                    else:
+                        snn.run_concurrent(nets, 700)
+                    for st in streams:
+                        stream.wait_stream(st)
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    form_trial[f + "_ms"] += a.elapsed_time(b)
+            form = "batch" if form_trial["batch_ms"] < form_trial["concurrent_ms"] else "concurrent"
+        chosen = [cfg_batch] * len(nets) if form == "batch" else cfg_conc
+        for n, c in zip(nets, chosen):
+            n.launch = c
     else:
         for n in nets:
             n.launch = {"l2_persist": args.l2_persist, **json.loads(args.launch)}
+        if nets[0].launch["path"] == 1 and not args.sequential:
+            form = "batch"
     steps = args.sim_steps
 
-    def bench_step():
-        if args.sequential:
-            for n in nets:
-                n.run(steps)
+    def advance(group, n_steps):
+        if form == "sequential":
+            for n in group:
+                n.run(n_steps)
+        elif form == "batch":
+            snn.run_batch(group, [n_steps] * len(group))
         else:
-            snn.run_concurrent(nets, steps)
+            snn.run_concurrent(group, n_steps)
+
+    def bench_step():
+        advance(nets, steps)
 
     for _ in range(args.warmup):
         bench_step()
@@ -410,26 +452,38 @@ def run_gb300(args, dist: Dist):
     # nodes around every kernel (the kernels' shares of the step: event nodes
     # lengthen each span, so only their ratio is used).  A kernel's launch
     # duration = step time x its share, both from the same steps, so launch
-    # gaps are charged to the kernels and `achieved` is a lower bound.
+    # gaps are charged to the kernels and `achieved` is a lower bound.  Four
+    # samples 1500 steps apart per network cover the slow oscillation of the
+    # SWA network (a single sample may fall in a Down state).  The algorithmic
+    # bytes per launch use the spike rate of the timed region itself.
     peak, peak_kind = measured_peaks()
-    kt, net_step_ms = [], []
+    n_samples, gap = 4, 1500
+    per_net = []
     for j, n in enumerate(nets):
         tk_steps = max(1, min(351, n.launch["window_steps"]))
-        s_a = n.stats()["spikes"]
-        tk = n.time_kernels(tk_steps)
-        spk_per_step = (n.stats()["spikes"] - s_a) / float(tk_steps)
+        t_upd = t_dl = t_step = 0.0
+        spk = 0
+        for i in range(n_samples):
+            if i:
+                n.run(gap)
+            s_a = n.stats()["spikes"]
+            tk = n.time_kernels(tk_steps)
+            spk += n.stats()["spikes"] - s_a
+            sh_u = tk["update_ms"] / (tk["update_ms"] + tk["deliver_ms"])
+            t_step += tk["step_ms"] * tk_steps
+            t_upd += tk["step_ms"] * sh_u * tk_steps
+            t_dl += tk["step_ms"] * (1.0 - sh_u) * tk_steps
+        ns = n_samples * tk_steps
         rec_bytes = 8 if n.params["record_format"] == W.REC_F32 else 6
-        upd_bytes = 26.0 * n.N
-        dl_bytes = spk_per_step * (n.M * rec_bytes + 8)
-        sh_u = tk["update_ms"] / (tk["update_ms"] + tk["deliver_ms"])
-        net_step_ms.append(tk["step_ms"])
-        tk_step = {"update_ms": tk["step_ms"] * sh_u, "deliver_ms": tk["step_ms"] * (1.0 - sh_u),
-                   "event_node_update_ms": tk["update_ms"], "event_node_deliver_ms": tk["deliver_ms"]}
-        kt.append((tk_step, upd_bytes, dl_bytes))
-    upd_ms = sum(k[0]["update_ms"] for k in kt) / len(kt)
-    dl_ms = sum(k[0]["deliver_ms"] for k in kt) / len(kt)
-    upd_b = sum(k[1] for k in kt) / len(kt)
-    dl_b = sum(k[2] for k in kt) / len(kt)
+        timed_spk_per_step = spikes[j] / float(args.steps * steps)
+        per_net.append({"step_ms": t_step / ns, "update_ms": t_upd / ns, "deliver_ms": t_dl / ns,
+                        "update_bytes": 26.0 * n.N,
+                        "deliver_bytes": timed_spk_per_step * (n.M * rec_bytes + 8),
+                        "timed_spikes_per_step": timed_spk_per_step, "sampled_spikes_per_step": spk / ns})
+    upd_ms = sum(x["update_ms"] for x in per_net) / len(per_net)
+    dl_ms = sum(x["deliver_ms"] for x in per_net) / len(per_net)
+    upd_b = sum(x["update_bytes"] for x in per_net) / len(per_net)
+    dl_b = sum(x["deliver_bytes"] for x in per_net) / len(per_net)
     kernels = {
         "k_update": {"ms_per_launch": upd_ms, "algorithmic_bytes": upd_b,
                      "achieved_gbs": upd_b / (upd_ms * 1e-3) / 1e9},
@@ -438,14 +492,39 @@ def run_gb300(args, dist: Dist):
     }
     dom = "k_update" if upd_ms >= dl_ms else "k_deliver"
     share = {k: v["ms_per_launch"] / (upd_ms + dl_ms) for k, v in kernels.items()}
+    method = (f"launch duration = ms per time step of the network alone ({n_samples} samples of 351 steps, {gap} "
+              f"steps apart, each as a graph timed with CUDA events) x the kernel's share of the same steps run "
+              f"again with event nodes; delivery bytes = timed-region spikes per step x (M x record bytes + 8)")
+    if form == "batch":
+        # the timed region ran one fused kernel per step for both networks:
+        # its launch duration is the timed region's time per step
+        fu_ms = 1e3 * elapsed / (args.steps * steps)
+        fu_b = sum(x["update_bytes"] + x["deliver_bytes"] for x in per_net)
+        kernels["k_fused"] = {"ms_per_launch": fu_ms, "algorithmic_bytes": fu_b,
+                              "achieved_gbs": fu_b / (fu_ms * 1e-3) / 1e9}
+        share["k_fused"] = 1.0
+        dom = "k_fused"
+        method = ("k_fused: one launch per step for both networks in the timed region; launch duration = timed "
+                  "region / steps (CUDA events on the launching stream), bytes = both networks' neuron state + "
+                  "timed-region spikes per step x (M x record bytes + 8).  k_update / k_deliver: the two-kernel "
+                  "path of each network alone, for reference (" + method + ")")
     ach = kernels[dom]["achieved_gbs"]
+    # the whole step, the unit a user sees: algorithmic bytes of a step (neuron
+    # state + every record delivered) over the step time, per network alone,
+    # and over the timed region for the job (both networks concurrently)
+    job_bytes = sum(26.0 * n.N * args.steps * steps for n in nets) + sum(
+        spikes[j] * (nets[j].M * (8 if nets[j].params["record_format"] == W.REC_F32 else 6) + 8)
+        for j in range(len(nets)))
+    step_frac = {names[j]: (x["update_bytes"] + x["deliver_bytes"]) / (x["step_ms"] * 1e-3) / 1e9 / peak
+                 for j, x in enumerate(per_net)}
+    step_frac["job"] = job_bytes / elapsed / 1e9 / peak
     roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "peak_kind": peak_kind, "traffic": committed_traffic(dom),
                 "share_of_step": share[dom],
-                "method": "launch duration = ms per time step of the network alone (the next 351 steps as a "
-                          "graph, CUDA events) x the kernel's share of the same steps run again with event nodes",
-
-                "step_ms": {names[j]: net_step_ms[j] for j in range(len(nets))},
+                "method": method,
+                "step_ms": {names[j]: x["step_ms"] for j, x in enumerate(per_net)},
+                "step_frac": step_frac,
+                "per_network": {names[j]: x for j, x in enumerate(per_net)},
                 "kernels": {k: {**v, "frac": v["achieved_gbs"] / peak, "share": share[k]} for k, v in kernels.items()}}
 
     # ---- activity of the simulated networks (host analysis of the binned rates, Sec. 2.3)
@@ -470,11 +549,9 @@ def run_gb300(args, dist: Dist):
             wl = W.grid_24x24(reg)
             e2e_nets.append(snn.Network(wl["params"], wl["seed"] + 104729 + 7919 * dist.rank,
                                         stream=streams[j].cuda_stream))
-        if args.sequential:
-            for n in e2e_nets:
-                n.run(e2e_steps)
-        else:
-            snn.run_concurrent(e2e_nets, e2e_steps)
+        for n, c in zip(e2e_nets, [n.launch for n in nets]):
+            n.launch = c
+        advance(e2e_nets, e2e_steps)
         for n in e2e_nets:
             st_, ids = n.spikes()
             rates = n.rates()
@@ -499,6 +576,21 @@ def run_gb300(args, dist: Dist):
                "sample": "oracle (plain C, 1 thread) on the same two 24x24 networks: 30 untimed steps, then 100 "
                          "timed steps of each (0.01 s simulated each)", "seconds": sec}
 
+    for n in nets:
+        n.close()
+    # ---- compact points of the other configurations, each with its own clocks
+    extras = None
+    if not args.no_extras and dist.world == 1:
+        extras = {
+            "grid64x64_aw_i16_lambda1": measure_grid64(snn, torch, dist, "AW", 1.0, W.REC_I16, timed=5000,
+                                                       transient=5000, trial_steps=100, analyse=False),
+        }
+        res, _, bnets = measure_batch(snn, torch, dist, n_nets=256, warm=2000, timed=5000, plain_timed=1000)
+        for n in bnets:
+            n.close()
+        extras["batch256"] = res
+        extras["serve200"] = measure_serve(snn, torch, dist, n_req=200, duration_scale=0.25, chunk_steps=1000)
+
     if dist.rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
@@ -510,8 +602,12 @@ def run_gb300(args, dist: Dist):
                        "l2": "inputs larger than L2 (2 x 6.5 GB synapse records); the neuron state and delay ring "
                              "of each network (~67 MB) stay in L2 across time steps by design",
                        "launch": [n.launch for n in nets], "parallelism": f"replicas x{dist.world}",
-                       "networks_run": "one after the other" if args.sequential
-                       else "concurrently, one CUDA stream each (snn_run_concurrent)"},
+                       "networks_run": {"sequential": "one after the other",
+                                        "concurrent": "concurrently, one CUDA stream each, two-kernel path "
+                                                      "(snn_run_concurrent)",
+                                        "batch": "together, one fused kernel per step for both networks "
+                                                 "(snn_run_batch)"}[form],
+                       "form_trial": form_trial},
             "sim_seconds_per_wall_second": sim_s * len(nets) * dist.world / t_max,
             "per_regime": {names[i]: {"spikes": spikes[i], "rate_hz": spikes[i] / (nets[i].N * sim_s),
                                       "recurrent_events": spikes[i] * W.OUT_DEGREE, "external_events": ext[i],
@@ -519,22 +615,24 @@ def run_gb300(args, dist: Dist):
                            for i in range(len(nets))},
             "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clocks,
             "paper_context": "2.3e9-4.1e9 equivalent synaptic events/s on up to 1024 Haswell cores (Abstract)",
+            "extra_configs": extras,
         }
         print(json.dumps(line), flush=True)
-    for n in nets:
-        n.close()
 
 
 # ---------------------------------------------------------------------------
 # batched sweep: one fused kernel per step over all networks vs one network per launch
 # ---------------------------------------------------------------------------
-def run_batch_mode(args, dist: Dist):
+def measure_batch(snn, torch, dist: Dist, n_nets: int, warm: int, timed: int, plain_timed: int,
+                  plain_nets: int | None = None) -> tuple[dict, list, list]:
+    """The batched sweep: `n_nets` networks on the fused path (one kernel per
+    step for all of them, shape from the batch tuner after `warm` steps), then
+    `timed` steps timed; beside it one network per launch (two kernels per
+    step, each network alone) on fresh copies of the first `plain_nets`
+    networks: their first `warm` steps compared with the batch's rasters, the
+    next `plain_timed` steps timed.  Returns (result, specs, batch networks)."""
     import numpy as np
-    import torch
-    torch.cuda.set_device(dist.local_rank)
-    import paper_1902_08410_gb300 as snn
-    snn.build()
-    specs = W.batched_sweep(n_nets=args.batch_nets, steps=args.batch_steps)
+    specs = W.batched_sweep(n_nets=n_nets, steps=timed)
     t0 = time.perf_counter()
     nets = [snn.Network(sp["params"], sp["seed"] + 7919 * dist.rank) for sp in specs]
     torch.cuda.synchronize()
@@ -544,7 +642,6 @@ def run_batch_mode(args, dist: Dist):
     stream = torch.cuda.current_stream()
     # the first steps (the initial volley) untimed, then the fused shape tuned
     # on the whole batch (state restored after the trials)
-    warm = args.plain_steps
     snn.run_batch(nets, [warm] * len(nets))
     tuned = snn.autotune_batch(nets, 200)
     st0 = sum(n.stats()["spikes"] for n in nets)
@@ -554,18 +651,15 @@ def run_batch_mode(args, dist: Dist):
     sampler = ClockSampler(gpu_selector(dist.local_rank))
     sampler.start()
     e0.record(stream)
-    snn.run_batch(nets, [args.batch_steps] * len(nets))
+    snn.run_batch(nets, [timed] * len(nets))
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
     t_batch = e0.elapsed_time(e1) / 1e3
     ev_batch = (sum(n.stats()["spikes"] for n in nets) - st0) * EQUIV_PER_SPIKE
-    neurons = sum(n.N for n in nets)
-    # one network per launch (two kernels per step, each network alone), fresh
-    # copies: the same first steps (rasters compared with the batch), then the
-    # next steps timed
-    ev_plain, t_plain, same = 0, 0.0, 0
-    for sp, bn in zip(specs, nets):
+    plain_nets = len(nets) if plain_nets is None else min(plain_nets, len(nets))
+    ev_plain, t_plain, same, ev_batch_sub = 0, 0.0, 0, 0
+    for sp, bn in zip(specs[:plain_nets], nets[:plain_nets]):
         n = snn.Network(sp["params"], sp["seed"] + 7919 * dist.rank)
         n.launch = {"path": 0}
         n.run(warm)
@@ -575,35 +669,49 @@ def run_batch_mode(args, dist: Dist):
         s0 = n.stats()["spikes"]
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        n.run(args.plain_steps)
+        n.run(plain_timed)
         b.record(stream)
         torch.cuda.synchronize()
         t_plain += a.elapsed_time(b) / 1e3
         ev_plain += (n.stats()["spikes"] - s0) * EQUIV_PER_SPIKE
         n.close()
-    batch_value, _ = job_throughput(dist, ev_batch, t_batch)
+    res = {
+        "workload": f"{len(nets)} networks, sides U{{2..8}}, g_c on a 16-point SWA->AW grid, nu_ext U[2, 8] Hz, "
+                    f"i16 records",
+        "neurons": sum(n.N for n in nets), "recurrent_synapses": sum(n.N * n.M for n in nets),
+        "batched": {"events_per_s": ev_batch / t_batch, "seconds": t_batch, "steps": timed,
+                    "us_per_step": 1e6 * t_batch / timed},
+        "one_network_per_launch": {"events_per_s": ev_plain / t_plain, "seconds": t_plain, "steps": plain_timed,
+                                   "networks": plain_nets},
+        "speedup": (ev_batch / t_batch) / (ev_plain / t_plain),
+        "identical_rasters": f"{same}/{plain_nets} networks (first {warm} steps, batched vs one per launch)",
+        "fused_launch": {k: tuned[k] for k in ("fused_block", "fused_items_per_sm", "deliver_lanes", "window_steps")},
+        "timing": f"both forms timed after the first {warm} steps of each network",
+        "build_seconds": build_s, "clocks": clocks,
+    }
+    return res, specs, nets
+
+
+def run_batch_mode(args, dist: Dist):
+    import torch
+    torch.cuda.set_device(dist.local_rank)
+    import paper_1902_08410_gb300 as snn
+    snn.build()
+    res, specs, nets = measure_batch(snn, torch, dist, args.batch_nets, args.plain_steps, args.batch_steps,
+                                     args.plain_steps)
+    for n in nets:
+        n.close()
+    batch_value, _ = job_throughput(dist, res["batched"]["events_per_s"] * res["batched"]["seconds"],
+                                    res["batched"]["seconds"])
     cpu = None
     if not args.no_cpu_baseline and dist.world == 1:
         cpu = oracle_all_cores(specs)
-    line = {
-        "metric": METRIC, "mode": "batch", "value": batch_value, "unit": UNIT,
-        "n_gpus": dist.world, "higher_is_better": True, "data": "synthetic", "dtype": "f32+i32",
-        "config": {"workload": f"{len(nets)} networks, sides U{{2..8}}, g_c on a 16-point SWA->AW grid, "
-                               f"nu_ext U[2, 8] Hz, i16 records, {args.batch_steps} steps each",
-                   "neurons": neurons, "recurrent_synapses": sum(n.N * n.M for n in nets)},
-        "batched": {"events_per_s": ev_batch / t_batch, "seconds": t_batch, "steps": args.batch_steps,
-                    "us_per_step": 1e6 * t_batch / args.batch_steps},
-        "one_network_per_launch": {"events_per_s": ev_plain / t_plain, "seconds": t_plain,
-                                   "steps": args.plain_steps},
-        "speedup": (ev_batch / t_batch) / (ev_plain / t_plain),
-        "identical_rasters": f"{same}/{len(nets)} networks (first {warm} steps)",
-        "fused_launch": {k: tuned[k] for k in ("fused_block", "fused_items_per_sm", "deliver_lanes", "window_steps")},
-        "timing": f"both forms timed after the first {warm} steps of each network",
-        "cpu_baseline": cpu,
-        "build_seconds": build_s, "clocks": clocks,
-    }
-    for n in nets:
-        n.close()
+    line = {"metric": METRIC, "mode": "batch", "value": batch_value, "unit": UNIT, "n_gpus": dist.world,
+            "higher_is_better": True, "data": "synthetic", "dtype": "f32+i32",
+            "config": {"workload": res["workload"] + f", {args.batch_steps} steps each", "neurons": res["neurons"],
+                       "recurrent_synapses": res["recurrent_synapses"]},
+            **{k: v for k, v in res.items() if k not in ("workload", "neurons", "recurrent_synapses")},
+            "cpu_baseline": cpu}
     if dist.rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -611,19 +719,19 @@ def run_batch_mode(args, dist: Dist):
 # ---------------------------------------------------------------------------
 # serving: Poisson-arrival stream of requests, continuous batching
 # ---------------------------------------------------------------------------
-def run_serve_mode(args, dist: Dist):
+def measure_serve(snn, torch, dist: Dist, n_req: int, duration_scale: float, chunk_steps: int,
+                  rate: float = 0.0) -> dict:
+    """Serve a Poisson-arrival stream of `n_req` requests (continuous batching,
+    admission by device-memory footprint); arrivals at `rate` requests/s, or at
+    0.8 x the batched capacity measured on the first requests after their
+    initial transient."""
     import numpy as np
-    import torch
-    torch.cuda.set_device(dist.local_rank)
-    import paper_1902_08410_gb300 as snn
     from paper_1902_08410_gb300.serve import Server
-    snn.build()
     free, total = torch.cuda.mem_get_info()
     budget = int(free * 0.8)
-    reqs = W.serving_requests(n_req=args.requests, rate_hz=1.0)
+    reqs = W.serving_requests(n_req=n_req, rate_hz=1.0)
     for r in reqs:
-        r["steps"] = max(1, int(round(r["steps"] * args.duration_scale)))
-    rate = args.rate
+        r["steps"] = max(1, int(round(r["steps"] * duration_scale)))
     if rate <= 0:
         # capacity: neuron-steps per second of the batched path on the first
         # requests, timed after their initial transient (the first steps fire a
@@ -641,21 +749,33 @@ def run_serve_mode(args, dist: Dist):
         work = np.mean([W.n_neurons(r["params"]) * r["steps"] for r in reqs])
         rate = 0.8 * rate_ns / work
     # arrivals: unit-rate stream rescaled to the chosen rate
-    srv = Server(memory_budget=budget, chunk_steps=args.chunk_steps, realtime=True)
+    srv = Server(memory_budget=budget, chunk_steps=chunk_steps, realtime=True)
     for r in reqs:
         srv.submit(r["params"], r["seed"], r["steps"], arrival_s=r["arrival_s"] / rate)
+    sampler = ClockSampler(gpu_selector(dist.local_rank))
+    sampler.start()
     out = srv.run()
+    clocks = sampler.stop()
     lat = np.array([x.latency_s for x in out["results"]])
-    line = {
-        "metric": "serving latency and aggregate synaptic events/s", "mode": "serve",
-        "p50_latency_s": out["p50_latency_s"], "p99_latency_s": out["p99_latency_s"],
-        "mean_latency_s": float(lat.mean()), "events_per_s": out["events_per_s"], "unit": UNIT,
-        "requests": len(reqs), "rate_per_s": rate, "wall_s": out["wall_s"], "chunks": out["chunks"],
-        "config": {"workload": f"{len(reqs)} requests, sides round(2^U(1,4)), durations U[0.5, 10] s x "
-                               f"{args.duration_scale}, SWA/AW 50/50, i16 records, Poisson arrivals",
-                   "memory_budget_bytes": budget, "chunk_steps": args.chunk_steps},
-        "data": "synthetic", "n_gpus": dist.world,
-    }
+    return {"p50_latency_s": out["p50_latency_s"], "p99_latency_s": out["p99_latency_s"],
+            "mean_latency_s": float(lat.mean()), "events_per_s": out["events_per_s"], "unit": UNIT,
+            "requests": len(reqs), "rate_per_s": rate, "wall_s": out["wall_s"], "chunks": out["chunks"],
+            "workload": f"{len(reqs)} requests, sides round(2^U(1,4)), durations U[0.5, 10] s x {duration_scale}, "
+                        f"SWA/AW 50/50, i16 records, Poisson arrivals",
+            "memory_budget_bytes": budget, "chunk_steps": chunk_steps, "clocks": clocks}
+
+
+def run_serve_mode(args, dist: Dist):
+    import torch
+    torch.cuda.set_device(dist.local_rank)
+    import paper_1902_08410_gb300 as snn
+    snn.build()
+    res = measure_serve(snn, torch, dist, args.requests, args.duration_scale, args.chunk_steps, args.rate)
+    line = {"metric": "serving latency and aggregate synaptic events/s", "mode": "serve",
+            **{k: v for k, v in res.items() if k not in ("workload", "memory_budget_bytes", "chunk_steps")},
+            "config": {"workload": res["workload"], "memory_budget_bytes": res["memory_budget_bytes"],
+                       "chunk_steps": res["chunk_steps"]},
+            "data": "synthetic", "n_gpus": dist.world}
     if dist.rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -716,51 +836,65 @@ def run_table_s1_mode(args, dist: Dist):
               flush=True)
 
 
-def run_grid64_mode(args, dist: Dist):
+def measure_grid64(snn, torch, dist: Dist, regime: str, lam: float, fmt: int, timed: int, transient: int = 5000,
+                   trial_steps: int = 300, analyse: bool = True) -> dict:
+    """One 64x64 network (5.12M neurons, 5.76G synapses): `transient` steps,
+    the tuner (trials of `trial_steps`), then `timed` steps timed with CUDA
+    events (clocks sampled meanwhile)."""
     import numpy as np
+    from paper_1902_08410_gb300 import analysis
+    wl = W.grid_64x64(regime, lam, fmt)
+    t0 = time.perf_counter()
+    net = snn.Network(wl["params"], wl["seed"])
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    net.run(transient)              # past the initial transient, where the tuner's choice would not hold
+    cfg = net.autotune(trial_steps)
+    st0 = net.stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(gpu_selector(dist.local_rank))
+    sampler.start()
+    e0.record()
+    net.run(timed)
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    sec = e0.elapsed_time(e1) / 1e3
+    st1 = net.stats()
+    spikes = st1["spikes"] - st0["spikes"]
+    sim_s = timed * W.DT_MS * 1e-3
+    rec_bytes = 8 if fmt == W.REC_F32 else 6
+    peak, _ = measured_peaks()
+    step_bytes = 26.0 * net.N + spikes / timed * (net.M * rec_bytes + 8)
+    out = {"format": "f32" if fmt == W.REC_F32 else "i16", "regime": regime, "lambda": lam,
+           "events_per_s": spikes * EQUIV_PER_SPIKE / sec, "sim_seconds_per_wall_second": sim_s / sec,
+           "us_per_step": 1e6 * sec / timed, "steps_timed": timed, "rate_hz": spikes / (net.N * sim_s),
+           "step_frac": step_bytes / (sec / timed) / 1e9 / peak,
+           "bytes_per_recurrent_synapse": st1["device_bytes"] / st1["n_synapses"],
+           "build_seconds": build_s, "launch": cfg, "clocks": clocks,
+           "timing": f"after {transient} steps and the tuner; {timed} steps, CUDA events"}
+    if analyse:
+        rates = net.rates()
+        pop = rates.sum(axis=(0, 1)).astype(np.float64)
+        dur = st1["t"] * W.DT_MS * 1e-3
+        out["pop_rate_hz"] = (pop / (np.array(W.POP_SIZES) * net.G * dur)).tolist()
+        out["swa_frequency_hz"] = analysis.dominant_frequency(rates, W.BIN_STEPS * W.DT_MS * 1e-3)
+        out["slow_waves"] = analysis.slow_wave_speeds(rates, 64, 64, W.BIN_STEPS * W.DT_MS * 1e-3, imd=IMD_MM,
+                                                      skip_s=0.5)
+    net.close()
+    return out
+
+
+def run_grid64_mode(args, dist: Dist):
     import torch
     torch.cuda.set_device(dist.local_rank)
     import paper_1902_08410_gb300 as snn
-    from paper_1902_08410_gb300 import analysis
     snn.build()
     runs = []
     for lam in [float(x) for x in args.grid64_lambdas.split(",")]:
         for reg in ("SWA", "AW"):
-            per_fmt = {}
-            for fmt in (W.REC_F32, W.REC_I16):
-                wl = W.grid_64x64(reg, lam, fmt)
-                t0 = time.perf_counter()
-                net = snn.Network(wl["params"], wl["seed"])
-                torch.cuda.synchronize()
-                build_s = time.perf_counter() - t0
-                net.run(5000)              # past the initial transient, where the tuner's choice would not hold
-                cfg = net.autotune(300)
-                st0 = net.stats()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                net.run(args.grid64_steps)
-                e1.record()
-                torch.cuda.synchronize()
-                sec = e0.elapsed_time(e1) / 1e3
-                st1 = net.stats()
-                spikes = st1["spikes"] - st0["spikes"]
-                sim_s = args.grid64_steps * W.DT_MS * 1e-3
-                rates = net.rates()
-                pop = rates.sum(axis=(0, 1)).astype(np.float64)
-                dur = st1["t"] * W.DT_MS * 1e-3
-                pop_hz = (pop / (np.array(W.POP_SIZES) * net.G * dur)).tolist()
-                per_fmt[fmt] = {
-                    "format": "f32" if fmt == W.REC_F32 else "i16", "events_per_s": spikes * EQUIV_PER_SPIKE / sec,
-                    "sim_seconds_per_wall_second": sim_s / sec, "us_per_step": 1e6 * sec / args.grid64_steps,
-                    "rate_hz": spikes / (net.N * sim_s), "pop_rate_hz": pop_hz,
-                    "swa_frequency_hz": analysis.dominant_frequency(rates, W.BIN_STEPS * W.DT_MS * 1e-3),
-                    "slow_waves": analysis.slow_wave_speeds(rates, 64, 64, W.BIN_STEPS * W.DT_MS * 1e-3,
-                                                            imd=IMD_MM, skip_s=0.5),
-                    "bytes_per_recurrent_synapse": st1["device_bytes"] / st1["n_synapses"],
-                    "build_seconds": build_s, "launch": cfg,
-                }
-                net.close()
-            f, q = per_fmt[W.REC_F32], per_fmt[W.REC_I16]
+            f = measure_grid64(snn, torch, dist, reg, lam, W.REC_F32, args.grid64_steps)
+            q = measure_grid64(snn, torch, dist, reg, lam, W.REC_I16, args.grid64_steps)
             runs.append({"lambda": lam, "regime": reg, "f32": f, "i16": q,
                          "i16_vs_f32": {"rate_delta_rel": q["rate_hz"] / f["rate_hz"] - 1.0,
                                         "swa_frequency_delta_hz": (None if f["swa_frequency_hz"] is None

@@ -195,6 +195,11 @@ int snn_set_launch(snn_handle h, const snn_launch *cfg);
  * restored afterwards, so results are unchanged. */
 int snn_autotune(snn_handle h, uint32_t trial_steps);
 
+/* The same with the launch path fixed: path 0 tunes the two-kernel path only
+ * (the shapes snn_run_concurrent can run), 1 the fused path only, -1 both
+ * (= snn_autotune).  The paper has no counterpart of the tuners. */
+int snn_autotune_path(snn_handle h, uint32_t trial_steps, int32_t path);
+
 /* The same for a batch advanced by snn_run_batch: fused-kernel shapes (block
  * size, blocks per SM, delivery chunk) are timed on the whole batch for
  * `trial_steps` steps each, from snapshots of every network (state, counters

@@ -208,8 +208,13 @@ class Network:
         c = SnnLaunch(**cur)
         _check(self._lib.snn_set_launch(self._h, ctypes.byref(c)))
 
-    def autotune(self, trial_steps: int = 200) -> dict:
-        _check(self._lib.snn_autotune(self._h, int(trial_steps)))
+    def autotune(self, trial_steps: int = 200, path: int | None = None) -> dict:
+        """Choose the launch shape (see snn_autotune); `path` 0 or 1 keeps the
+        tuner on that launch path (snn_autotune_path)."""
+        if path is None:
+            _check(self._lib.snn_autotune(self._h, int(trial_steps)))
+        else:
+            _check(self._lib.snn_autotune_path(self._h, int(trial_steps), int(path)))
         return self.launch
 
     def time_kernels(self, steps: int) -> dict:

@@ -105,7 +105,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 # every symbol declared in include/snn.h
 EXPORTS = ["snn_set_allocator", "snn_footprint", "snn_build_network", "snn_run", "snn_run_batch",
            "snn_read_spikes", "snn_rates", "snn_read_state", "snn_read_row", "snn_get_stats",
-           "snn_get_launch", "snn_set_launch", "snn_autotune", "snn_free", "snn_last_error",
+           "snn_get_launch", "snn_set_launch", "snn_autotune", "snn_autotune_path", "snn_free", "snn_last_error",
            "snn_time_kernels", "snn_build_rows_static", "snn_run_concurrent",
            "snn_autotune_batch"]
 
@@ -139,6 +139,7 @@ def load(build_if_needed: bool = True):
         "snn_get_launch": ([vp, P(SnnLaunch)], ctypes.c_int),
         "snn_set_launch": ([vp, P(SnnLaunch)], ctypes.c_int),
         "snn_autotune": ([vp, u32], ctypes.c_int),
+        "snn_autotune_path": ([vp, u32, i32], ctypes.c_int),
         "snn_autotune_batch": ([P(vp), i32, u32], ctypes.c_int),
         "snn_free": ([vp], None),
         "snn_last_error": ([], ctypes.c_char_p),

@@ -1503,13 +1503,15 @@ extern "C" int snn_set_launch(snn_handle h, const snn_launch *cfg) {
 // autotuner: time candidate shapes from a snapshot of the state, restore the
 // snapshot after each trial, so the network's results are unchanged.
 // ---------------------------------------------------------------------------
-extern "C" int snn_autotune(snn_handle h, uint32_t trial_steps) {
+// path_only: -1 = both launch paths, 0 = two-kernel path only, 1 = fused only.
+static int autotune_impl(snn_net *h, uint32_t trial_steps, int path_only) {
   if (!h) return fail(SNN_ERR_ARG, "null handle");
   if (h->broken) return fail(SNN_ERR_STATE, "network is invalid after an earlier failure");
   if (trial_steps == 0) return fail(SNN_ERR_ARG, "trial_steps must be > 0");
+  if (path_only < -1 || path_only > 1) return fail(SNN_ERR_ARG, "path must be -1, 0 or 1");
   const Layout &L = h->L;
   uint8_t *base = static_cast<uint8_t *>(h->arena.p);
-  const size_t state_bytes = L.off_rows;   // V, c, ref, ring
+  const size_t state_bytes = L.off_rows;   // V, c, ref, input buffers, spike history
   DevBuf snap;
   int rc = dev_alloc(snap, state_bytes);
   if (rc) return rc;
@@ -1526,13 +1528,16 @@ extern "C" int snn_autotune(snn_handle h, uint32_t trial_steps) {
   const uint64_t t_saved = h->t, spikes_saved = h->spikes, ext_saved = h->ext_events;
   const size_t raster_saved = h->raster.size(), sorted_saved = h->raster_sorted;
   const std::vector<uint32_t> rates_saved = h->rates;
-  const snn_launch orig = h->cfg;
+  const snn_launch saved_cfg = h->cfg;
+  snn_launch orig = h->cfg;   // the incumbent, on the allowed path
+  if (path_only >= 0) orig.path = path_only;
 
   // stage 1: update shapes with the current delivery shape, and the fused path
   std::vector<snn_launch> cands;
   for (int ub : {64, 128, 256})
     for (int ug : {1, 2, 4}) {
       if (ub == 64 && ug != 1) continue;
+      if (path_only == 1) continue;
       snn_launch c = orig;
       c.path = 0;
       c.update_block = ub;
@@ -1542,6 +1547,7 @@ extern "C" int snn_autotune(snn_handle h, uint32_t trial_steps) {
   for (int fb : {128, 256})
     for (int ips : {4, 8, 16})
       for (int ln : {8, 16}) {
+        if (path_only == 0) continue;
         snn_launch c = orig;
         c.path = 1;
         c.fused_block = fb;
@@ -1637,6 +1643,12 @@ extern "C" int snn_autotune(snn_handle h, uint32_t trial_steps) {
   h->raster.resize(raster_saved);
   h->raster_sorted = std::min(sorted_saved, raster_saved);
   h->rates = rates_saved;
-  h->cfg = (status == SNN_OK) ? best : orig;
+  h->cfg = (status == SNN_OK) ? best : saved_cfg;
   return status;
+}
+
+extern "C" int snn_autotune(snn_handle h, uint32_t trial_steps) { return autotune_impl(h, trial_steps, -1); }
+
+extern "C" int snn_autotune_path(snn_handle h, uint32_t trial_steps, int32_t path) {
+  return autotune_impl(h, trial_steps, path);
 }

@@ -1,9 +1,11 @@
 """Bit-exact parity with the oracle on the benchmarked configurations, at length.
 
 * 24x24 grid (720k neurons, 0.81G synapses, lambda 1.0, f32 records), the SWA and
-  the AW network: 2400 steps each, advanced the way the benchmark advances them
-  (the default launch shape first, then the shape the tuner picks, then both
-  networks concurrently on their own streams through snn_run_concurrent).
+  the AW network: 2400 steps each, advanced in both ways the benchmark can
+  advance them (the default launch shape alone first, then the two-kernel
+  shape the tuner picks with both networks concurrently on their own streams
+  through snn_run_concurrent, then both in one fused kernel per step with the
+  shape the batch tuner picks, through snn_run_batch).
 * 64x64 grid (5.12M neurons, 5.76G synapses, AW, lambda 1.0): 250 steps on both
   record formats, tuned after the first 100 steps.
 * 8x8 grid over the full 2 s of the batched sweep (20,000 steps, SWA, i16
@@ -26,7 +28,7 @@ from parity import assert_same, gpu_results
 
 pytestmark = pytest.mark.gpu
 
-C2_STEPS, C2_ALONE = 2400, 600
+C2_STEPS, C2_ALONE, C2_CONCURRENT = 2400, 600, 900
 C3_STEPS, C3_TUNE_AT = 250, 100
 C4_STEPS, C4_TUNE_AT = 20_000, 2000
 COMPANION_STEPS = 7000
@@ -81,8 +83,8 @@ def _oracle(futs, key):
     return futs[key].result(timeout=1500)
 
 
-def test_grid24x24_swa_aw_concurrent_tuned(snn, oracle_runs):
-    """Both 24x24 networks as the benchmark runs them."""
+def test_grid24x24_swa_aw_as_benchmarked(snn, oracle_runs):
+    """Both 24x24 networks as the benchmark runs them, in both forms."""
     import torch
     nets = []
     for reg in ("SWA", "AW"):
@@ -95,8 +97,11 @@ def test_grid24x24_swa_aw_concurrent_tuned(snn, oracle_runs):
     assert default["path"] == 0 and default["l2_persist"] == 1
     for g in nets:
         g.run(C2_ALONE)
-        g.autotune(50)
-    snn.run_concurrent(nets, C2_STEPS - C2_ALONE)
+        g.autotune(50, path=0)
+    snn.run_concurrent(nets, C2_CONCURRENT)
+    cfg = snn.autotune_batch(nets, 50)
+    assert cfg["path"] == 1
+    snn.run_batch(nets, [C2_STEPS - C2_ALONE - C2_CONCURRENT] * 2)
     for g, reg in zip(nets, ("SWA", "AW")):
         assert_same(gpu_results(g), _oracle(oracle_runs, f"c2_{reg}"), C2_STEPS, f"24x24 {reg}")
         g.close()
