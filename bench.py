@@ -576,6 +576,7 @@ def run_gb300(args, dist: Dist):
                "sample": "oracle (plain C, 1 thread) on the same two 24x24 networks: 30 untimed steps, then 100 "
                          "timed steps of each (0.01 s simulated each)", "seconds": sec}
 
+    launch_cfgs = [n.launch for n in nets]
     for n in nets:
         n.close()
     # ---- compact points of the other configurations, each with its own clocks
@@ -601,7 +602,7 @@ def run_gb300(args, dist: Dist):
                        "sim_seconds_per_step_per_network": steps * W.DT_MS * 1e-3,
                        "l2": "inputs larger than L2 (2 x 6.5 GB synapse records); the neuron state and delay ring "
                              "of each network (~67 MB) stay in L2 across time steps by design",
-                       "launch": [n.launch for n in nets], "parallelism": f"replicas x{dist.world}",
+                       "launch": launch_cfgs, "parallelism": f"replicas x{dist.world}",
                        "networks_run": {"sequential": "one after the other",
                                         "concurrent": "concurrently, one CUDA stream each, two-kernel path "
                                                       "(snn_run_concurrent)",
