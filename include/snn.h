@@ -10,7 +10,7 @@
  * efficacies are Gaussian (mean J, SD dJ_frac*|J|); every neuron also receives a
  * Poisson drive of N_ext trains at nu_ext with Gaussian amplitudes (Sec. 2.1,
  * Table S1).  The simulation is time driven with dt = dt_ms, delays of
- * 1..n_delay steps, and synaptic input accumulated in int32 fixed point of
+ * min_delay..n_delay steps, and synaptic input accumulated in int32 fixed point of
  * 2^-16 mV, so spike rasters do not depend on delivery order.
  *
  * Conventions:
@@ -56,7 +56,11 @@ typedef struct snn_params {
                               module, the rest over the other modules ~ exp(-d/lambda);
                               < 0: pure Eq. 1 kernel over all modules, source included */
   int32_t out_degree;      /* M, synapses per neuron (1125) */
-  int32_t n_delay;         /* delays uniform on 1..n_delay steps (1..254) */
+  int32_t n_delay;         /* largest delay in steps (1..254) */
+  int32_t min_delay;       /* smallest delay in steps (1..n_delay; 0 is read as 1): delays are
+                              uniform on min_delay..n_delay.  The spikes of min_delay
+                              consecutive steps are delivered in one pass (Sec. 2.1.1: the
+                              exchange step equals the minimum delay) */
   float dt_ms;             /* time step (0.1 ms) */
   int32_t record_format;   /* SNN_REC_F32 or SNN_REC_I16 */
   int32_t bin_steps;       /* steps per rate bin (50 = 5 ms, Sec. 2.3) */
@@ -153,7 +157,10 @@ int snn_run(snn_handle h, uint64_t steps);
 /* Advance n networks together by steps[i] each with one fused kernel per time
  * step over all of them (networks that reach their count stop early).  Each
  * network's results are identical to snn_run on it alone.  The networks must
- * share one device; the call is ordered on the first network's stream. */
+ * share one device; the call is ordered on the first network's stream.
+ * Errors as snn_run, plus SNN_ERR_ARG (a network twice or NULL) and
+ * SNN_ERR_LIMIT (more than 65535 networks).  The paper has no counterpart:
+ * batching independent networks is a systems pattern of this library. */
 int snn_run_batch(const snn_handle *hs, const uint64_t *steps, int32_t n);
 
 /* Advance n networks by steps[i] each on the two-kernel path (launch path 0
@@ -162,28 +169,42 @@ int snn_run_batch(const snn_handle *hs, const uint64_t *steps, int32_t n);
  * networks run at the same time when their streams differ (networks sharing a
  * stream run one after the other).  Each network's results
  * are identical to snn_run on it alone.  Returns after all steps completed and
- * their records reached host memory.  n in 1..1024. */
+ * their records reached host memory.  n in 1..1024.  The paper has no
+ * counterpart (one MPI job simulates one network). */
 int snn_run_concurrent(const snn_handle *hs, const uint64_t *steps, int32_t n);
 
-/* Spikes with t0 <= step < t1, ordered by (step, id), as two parallel host
- * arrays of capacity `cap`.  *n_out receives the count; if it exceeds cap
- * nothing is written and SNN_ERR_BUFFER is returned. */
+/* The spike raster (Sec. 2.3: the spikes every analysis starts from): spikes
+ * with t0 <= step < t1, ordered by (step, id), as two parallel host arrays of
+ * capacity `cap` owned by the caller (either may be NULL when cap is 0, to
+ * query the count).  *n_out receives the count; if it exceeds cap nothing is
+ * written and SNN_ERR_BUFFER is returned.  The raster is held in host memory
+ * by the library, so the call does not touch the device. */
 int snn_read_spikes(snn_handle h, uint64_t t0, uint64_t t1, uint32_t *step_out, uint32_t *id_out,
                     size_t cap, size_t *n_out);
 
 /* Spike counts per (bin, module, population) for all completed steps, layout
- * [bin][module][F, B, I], bin = step / bin_steps (Sec. 2.3 rates; Hz =
- * count / (population size * bin_steps * dt)).  *n_out = bins * G * 3. */
+ * [bin][module][F, B, I], bin = step / bin_steps (Sec. 2.3: population rates
+ * in 5 ms bins; Hz = count / (population size * bin_steps * dt)).  The bin
+ * width is the network's parameter bin_steps, fixed at build: the counts are
+ * accumulated on the device while the steps run (other widths: bin the raster
+ * of snn_read_spikes).  *n_out = bins * G * 3; SNN_ERR_BUFFER when cap is
+ * smaller (nothing written). */
 int snn_rates(snn_handle h, uint32_t *counts_out, size_t cap, size_t *n_out);
 
-/* Copy the neuron state (V in mV, c in mV, remaining refractory steps) of all
- * N neurons to host arrays of length n >= N. */
+/* Copy the neuron state of Eq. 2 (V in mV, c in mV, remaining refractory
+ * steps) of all N neurons to caller-owned host arrays of length n >= N (any of
+ * them may be NULL).  Refractory counters are stored as 8-bit values on the
+ * device and widened to int32 here.  Synchronises the network's stream. */
 int snn_read_state(snn_handle h, float *V_out, float *c_out, int32_t *ref_out, size_t n);
 
-/* Copy the stored outgoing row of source neuron s: M record keys
- * (delay << 24 | target) and weights in mV (for SNN_REC_I16, q * 2^-10). */
+/* Copy the stored outgoing row of source neuron s (Eq. 1 construction,
+ * Sec. 2.2 efficacies): M record keys (delay << 24 | target) in stored order
+ * and weights in mV (for SNN_REC_I16, q * 2^-10) into caller arrays of
+ * capacity cap >= M.  Synchronises the network's stream. */
 int snn_read_row(snn_handle h, uint32_t s, uint32_t *keys_out, float *w_out, size_t cap);
 
+/* Counters of the network (host memory; no device access).  Events follow the
+ * paper's equivalent-event count (Sec. 2.4) when multiplied by M + N_ext. */
 int snn_get_stats(snn_handle h, snn_stats *out);
 
 /* Launch shapes (results never depend on them). */

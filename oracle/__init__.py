@@ -43,7 +43,7 @@ class Params(ctypes.Structure):
     _fields_ = [
         ("gx", ctypes.c_int32), ("gy", ctypes.c_int32),
         ("lambda_", ctypes.c_float), ("p_local", ctypes.c_float),
-        ("out_degree", ctypes.c_int32), ("n_delay", ctypes.c_int32),
+        ("out_degree", ctypes.c_int32), ("n_delay", ctypes.c_int32), ("min_delay", ctypes.c_int32),
         ("dt_ms", ctypes.c_float), ("record_format", ctypes.c_int32),
         ("bin_steps", ctypes.c_int32),
         ("tau_m", ctypes.c_float * 3), ("C_m", ctypes.c_float * 3), ("E_L", ctypes.c_float * 3),
@@ -62,6 +62,7 @@ def make_params(d: dict) -> Params:
     p.p_local = float(d["p_local"])
     p.out_degree = int(d["out_degree"])
     p.n_delay = int(d["n_delay"])
+    p.min_delay = int(d.get("min_delay", 1))
     p.dt_ms = float(d["dt_ms"])
     p.record_format = int(d["record_format"])
     p.bin_steps = int(d["bin_steps"])

@@ -64,6 +64,7 @@ typedef struct {
   float p_local;        /* >= 0: share of excitatory out-degree kept local; < 0: pure Eq. 1 */
   int32_t out_degree;
   int32_t n_delay;
+  int32_t min_delay;    /* delays uniform on min_delay..n_delay (0 is read as 1) */
   float dt_ms;
   int32_t record_format;
   int32_t bin_steps;
@@ -247,8 +248,9 @@ static int32_t orc_pick_module(const uint32_t *T, int32_t G, uint32_t u) {
 }
 
 /* Synapse j of source s: target module (Eq. 1), target neuron uniform in the
- * module, delay, and efficacy Gaussian around J (Sec. 2.2), from one Philox
- * call. */
+ * module, delay uniform on min_delay..n_delay steps (the paper fixes only the
+ * minimum delay, Sec. 2.1.1), and efficacy Gaussian around J (Sec. 2.2), from
+ * one Philox call. */
 void orc_synapse(const orc_net *net, uint32_t s, uint32_t j, uint32_t *key, float *w) {
   const orc_params *P = &net->p;
   uint32_t r[4];
@@ -260,7 +262,8 @@ void orc_synapse(const orc_net *net, uint32_t s, uint32_t j, uint32_t *key, floa
   else mt = orc_pick_module(net->cdf + (size_t)ms * (size_t)(net->G - 1), net->G, r[0]);
   uint32_t lt = (uint32_t)(((uint64_t)r[1] * (uint64_t)ORC_K) >> 32);
   uint32_t tgt = (uint32_t)mt * ORC_K + lt;
-  uint32_t d = 1u + (uint32_t)(((uint64_t)r[2] * (uint64_t)P->n_delay) >> 32);
+  uint32_t dmin = P->min_delay < 1 ? 1u : (uint32_t)P->min_delay;
+  uint32_t d = dmin + (uint32_t)(((uint64_t)r[2] * (uint64_t)(P->n_delay - (int32_t)dmin + 1)) >> 32);
   int tp = orc_pop_of((int32_t)lt);
   float J = P->J[tp][sp];
   float sig = P->dJ_frac * fabsf(J);
@@ -435,6 +438,7 @@ void orc_destroy(orc_net *net) {
 
 orc_net *orc_create(const orc_params *P, uint64_t seed) {
   if (P->gx < 1 || P->gy < 1 || P->out_degree < 1 || P->n_delay < 1 || P->n_delay > 255 ||
+      P->min_delay < 0 || P->min_delay > P->n_delay ||
       P->bin_steps < 1 || !(P->dt_ms > 0.0f) || !(P->lambda > 0.0f))
     return NULL;
   orc_net *net = (orc_net *)calloc(1, sizeof(orc_net));

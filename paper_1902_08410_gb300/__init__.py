@@ -50,6 +50,7 @@ def make_params(d: dict) -> SnnParams:
     p.p_local = float(d["p_local"])
     p.out_degree = int(d["out_degree"])
     p.n_delay = int(d["n_delay"])
+    p.min_delay = int(d.get("min_delay", 1))
     p.dt_ms = float(d["dt_ms"])
     p.record_format = int(d["record_format"])
     p.bin_steps = int(d["bin_steps"])

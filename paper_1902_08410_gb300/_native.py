@@ -72,7 +72,7 @@ class SnnParams(ctypes.Structure):
     _fields_ = [
         ("gx", ctypes.c_int32), ("gy", ctypes.c_int32),
         ("lambda_", ctypes.c_float), ("p_local", ctypes.c_float),
-        ("out_degree", ctypes.c_int32), ("n_delay", ctypes.c_int32),
+        ("out_degree", ctypes.c_int32), ("n_delay", ctypes.c_int32), ("min_delay", ctypes.c_int32),
         ("dt_ms", ctypes.c_float), ("record_format", ctypes.c_int32),
         ("bin_steps", ctypes.c_int32),
         ("tau_m", ctypes.c_float * 3), ("C_m", ctypes.c_float * 3), ("E_L", ctypes.c_float * 3),

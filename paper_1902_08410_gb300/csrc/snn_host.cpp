@@ -249,6 +249,7 @@ void build_inputs(const snn_params &p, BuildDev &bd) {
       bd.sig[a][b] = p.dJ_frac * std::fabs(p.J[a][b]);
     }
   bd.n_delay = (uint32_t)p.n_delay;
+  bd.min_delay = (uint32_t)(p.min_delay < 1 ? 1 : p.min_delay);
   bd.p_local_mode = p.p_local >= 0.0f ? 1 : 0;
 }
 
@@ -269,7 +270,7 @@ struct Layout {
   size_t off_win[2], off_rec[2], off_ext[2], off_rates[2], off_entries[2];
   size_t rec_block;   // bytes of one recording block
   size_t total;
-  uint32_t N, N_pad, G, M, M_pad, D, row_bytes, os;
+  uint32_t N, N_pad, G, M, M_pad, D, row_bytes, os, kmin, nbuf;
   uint32_t window, rates_bins, rec_cap, n_ext_slots;
 };
 
@@ -284,6 +285,7 @@ int snn_validate_params(const snn_params &p) {
   if (p.out_degree < 1) return fail(SNN_ERR_ARG, "out_degree must be >= 1");
   if (p.out_degree > 2048) return fail(SNN_ERR_LIMIT, "out_degree above 2048");
   if (p.n_delay < 1 || p.n_delay > 254) return fail(SNN_ERR_ARG, "n_delay must be in 1..254");
+  if (p.min_delay < 0 || p.min_delay > p.n_delay) return fail(SNN_ERR_ARG, "min_delay must be in 0..n_delay");
   if (!(p.dt_ms > 0.0f)) return fail(SNN_ERR_ARG, "dt_ms must be > 0");
   if (p.record_format != SNN_REC_F32 && p.record_format != SNN_REC_I16) return fail(SNN_ERR_ARG, "unknown record_format");
   if (p.bin_steps < 1) return fail(SNN_ERR_ARG, "bin_steps must be >= 1");
@@ -307,7 +309,9 @@ static Layout make_layout(const snn_params &p) {
   L.N_pad = (uint32_t)align_up(L.N, kNeuronAlign);
   L.M = (uint32_t)p.out_degree;
   L.M_pad = (uint32_t)align_up(L.M, 8);
-  L.D = (uint32_t)p.n_delay + 1u;
+  L.kmin = (uint32_t)(p.min_delay < 1 ? 1 : p.min_delay);
+  L.nbuf = L.kmin + 1u;
+  L.D = (uint32_t)p.n_delay + L.kmin;
   L.row_bytes = L.M_pad * 4u + L.M_pad * (p.record_format == SNN_REC_I16 ? 2u : 4u);
   L.os = offs_stride((uint32_t)p.n_delay);
   L.n_ext_slots = L.N_pad / 128u;
@@ -332,8 +336,8 @@ static Layout make_layout(const snn_params &p) {
   L.off_V = take((size_t)L.N_pad * 4);
   L.off_c = take((size_t)L.N_pad * 4);
   L.off_ref = take((size_t)L.N_pad);
-  L.off_acc_loc = take((size_t)2 * L.N_pad * 4);
-  L.off_acc_rem = take((size_t)2 * L.N_pad * 4);
+  L.off_acc_loc = take((size_t)L.nbuf * L.N_pad * 4);
+  L.off_acc_rem = take((size_t)L.nbuf * L.N_pad * 4);
   L.off_hcnt = take((size_t)L.D * L.G * 4);
   L.off_hist = take((size_t)L.D * L.N * 4);
   L.off_rows = take((size_t)L.N * L.row_bytes);
@@ -368,7 +372,10 @@ struct snn_net {
   cudaStream_t copy_stream = nullptr;   // raster entry copies while the next window runs
   cudaEvent_t ev_block[2] = {nullptr, nullptr};   // recording block b copied to the host
   snn_launch cfg{};
-  cudaGraphExec_t exec[2] = {nullptr, nullptr};   // one graph per buffer set
+  // window graphs of the two-kernel path, per buffer set and phase of the
+  // window's first step within an exchange period (t0 % kmin), captured lazily
+  std::vector<cudaGraphExec_t> exec[2];
+  std::vector<uint32_t> exec_kernels[2];   // kernels launched by each graph
   uint32_t exec_window = 0;
   snn_launch exec_cfg{};
   float exec_l2_ratio = -1.0f;       // hit ratio baked into the captured graphs
@@ -496,7 +503,8 @@ static void free_net(snn_net *h) {
   if (!h) return;
   l2_release(h);
   for (int b = 0; b < 2; ++b) {
-    if (h->exec[b]) cudaGraphExecDestroy(h->exec[b]);
+    for (auto e : h->exec[b])
+      if (e) cudaGraphExecDestroy(e);
     if (h->ev_block[b]) cudaEventDestroy(h->ev_block[b]);
   }
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -538,6 +546,8 @@ static void fill_descriptor(snn_net *h) {
   d.rates_bins = L.rates_bins;
   d.n_delay = (uint32_t)h->p.n_delay;
   d.os = L.os;
+  d.kmin = L.kmin;
+  d.nbuf = L.nbuf;
   for (int q = 0; q < 3; ++q) {
     const PopTables t = pop_tables(h->p, q);
     d.pvv[q] = t.pvv;
@@ -663,43 +673,76 @@ extern "C" int snn_build_network(const snn_params *p, uint64_t seed, void *cuda_
 // ---------------------------------------------------------------------------
 // windows of steps
 // ---------------------------------------------------------------------------
-static int capture_window(snn_net *h, uint32_t window) {
+// Drop the cached window graphs unless they were captured for this window
+// length, launch shape and L2 window.
+static int prepare_graphs(snn_net *h, uint32_t window) {
   L2Window l2;   // set-aside changes are not allowed while a capture is open
   int rc = l2_window(h, &l2);
   if (rc) return rc;
-  if (h->exec[0] && h->exec[1] && h->exec_window == window && h->exec_l2_ratio == l2.hit_ratio &&
-      std::memcmp(&h->exec_cfg, &h->cfg, sizeof(snn_launch)) == 0)
+  if (h->exec_window == window && h->exec_l2_ratio == l2.hit_ratio &&
+      std::memcmp(&h->exec_cfg, &h->cfg, sizeof(snn_launch)) == 0 && h->exec[0].size() == h->L.kmin)
     return SNN_OK;
-  for (int b = 0; b < 2; ++b)
-    if (h->exec[b]) {
-      cudaGraphExecDestroy(h->exec[b]);
-      h->exec[b] = nullptr;
-    }
-  const snn_launch &c = h->cfg;
-  cudaStream_t cs = h->cap_stream;
   for (int b = 0; b < 2; ++b) {
-    const NetDev d = descriptor(h, b);
-    CU_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    cudaError_t err = cudaSuccess;
-    for (uint32_t k = 0; k < window && err == cudaSuccess; ++k) {
-      err = launch_update(d, k, c.update_block, c.update_groups, l2, cs);
-      if (err == cudaSuccess)
-        err = launch_deliver(d, k, (uint32_t)c.deliver_lanes, c.deliver_warps, deliver_grid(h), l2, cs);
-    }
-    cudaGraph_t g = nullptr;
-    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
-    if (err != cudaSuccess) {
-      if (g) cudaGraphDestroy(g);
-      return fail(SNN_ERR_CUDA, std::string("kernel launch during capture: ") + cudaGetErrorString(err));
-    }
-    if (e2 != cudaSuccess) return fail(SNN_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e2));
-    cudaError_t e3 = cudaGraphInstantiate(&h->exec[b], g, 0);
-    cudaGraphDestroy(g);
-    if (e3 != cudaSuccess) return fail(SNN_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e3));
+    for (auto e : h->exec[b])
+      if (e) cudaGraphExecDestroy(e);
+    h->exec[b].assign(h->L.kmin, nullptr);
+    h->exec_kernels[b].assign(h->L.kmin, 0u);
   }
   h->exec_window = window;
   h->exec_cfg = h->cfg;
   h->exec_l2_ratio = l2.hit_ratio;
+  return SNN_OK;
+}
+
+// Capture the steps k = 0..steps-1 of a window starting at a step with
+// phase = t0 % kmin: the update of every step, the delivery pass after every
+// step t with (t + 1) % kmin == 0.  With `ev`, event record nodes bracket every
+// kernel (ev[4k..4k+3]: update start/end, delivery start/end).
+static int capture_steps(snn_net *h, const NetDev &d, uint32_t steps, uint32_t phase, const L2Window &l2,
+                         cudaEvent_t *ev, cudaGraphExec_t *out, uint32_t *kernels) {
+  const snn_launch &c = h->cfg;
+  cudaStream_t cs = h->cap_stream;
+  CU_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  cudaError_t err = cudaSuccess;
+  uint32_t n = 0;
+  for (uint32_t k = 0; k < steps && err == cudaSuccess; ++k) {
+    if (ev) err = cudaEventRecordWithFlags(ev[4 * k + 0], cs, cudaEventRecordExternal);
+    if (err == cudaSuccess) err = launch_update(d, k, c.update_block, c.update_groups, l2, cs);
+    ++n;
+    if (ev && err == cudaSuccess) err = cudaEventRecordWithFlags(ev[4 * k + 1], cs, cudaEventRecordExternal);
+    if ((phase + k + 1u) % h->L.kmin == 0u) {
+      if (ev && err == cudaSuccess) err = cudaEventRecordWithFlags(ev[4 * k + 2], cs, cudaEventRecordExternal);
+      if (err == cudaSuccess)
+        err = launch_deliver(d, k, (uint32_t)c.deliver_lanes, c.deliver_warps, deliver_grid(h), l2, cs);
+      ++n;
+      if (ev && err == cudaSuccess) err = cudaEventRecordWithFlags(ev[4 * k + 3], cs, cudaEventRecordExternal);
+    }
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+  if (err != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(SNN_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(err != cudaSuccess ? err : e2));
+  }
+  cudaError_t e3 = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e3 != cudaSuccess) return fail(SNN_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e3));
+  if (kernels) *kernels = n;
+  return SNN_OK;
+}
+
+// The window graph of buffer set b for windows starting at phase `phase`.
+static int window_graph(snn_net *h, int b, uint32_t phase, cudaGraphExec_t *out, uint32_t *kernels) {
+  if (!h->exec[b][phase]) {
+    L2Window l2;
+    int rc = l2_window(h, &l2);
+    if (rc) return rc;
+    rc = capture_steps(h, descriptor(h, b), h->exec_window, phase, l2, nullptr, &h->exec[b][phase],
+                       &h->exec_kernels[b][phase]);
+    if (rc) return rc;
+  }
+  *out = h->exec[b][phase];
+  *kernels = h->exec_kernels[b][phase];
   return SNN_OK;
 }
 
@@ -844,11 +887,15 @@ static int runner_issue(PlainRunner &r) {
   pw->t0 = (uint32_t)t0;
   pw->t_end = (uint32_t)(t0 + n);
   pw->bin0 = (uint32_t)(t0 / (uint64_t)h->p.bin_steps);
+  cudaGraphExec_t gx = nullptr;
+  uint32_t kernels = 0;
+  int rc = window_graph(h, b, (uint32_t)(t0 % h->L.kmin), &gx, &kernels);
+  if (rc) return rc;
   CU_TRY(cudaMemcpyAsync(base + h->L.off_win[b], pw, sizeof(NetWin), cudaMemcpyHostToDevice, h->stream));
-  CU_TRY(cudaGraphLaunch(h->exec[b], h->stream));
+  CU_TRY(cudaGraphLaunch(gx, h->stream));
   h->h2d += sizeof(NetWin);
-  h->launches += 2ull * r.window;
-  int rc = drain_copy_block(h, b, h->stream);
+  h->launches += kernels;
+  rc = drain_copy_block(h, b, h->stream);
   if (rc) return rc;
   r.q[r.nq++] = PlainRunner::Pending{b, t0, n};
   r.next_b ^= 1;
@@ -872,7 +919,7 @@ static int run_plain(snn_net *h, uint64_t steps) {
   r.window = plain_window(h);
   r.steps = steps;
   r.t_issue = h->t;
-  int rc = capture_window(h, r.window);
+  int rc = prepare_graphs(h, r.window);
   if (rc) return rc;
   int status = SNN_OK;
   while (status == SNN_OK && r.busy()) status = r.can_issue() ? runner_issue(r) : runner_drain(r);
@@ -891,7 +938,7 @@ static int run_plain_many(snn_net *const *hs, const uint64_t *steps, int32_t n) 
     rs[i].steps = steps[i];
     rs[i].t_issue = hs[i]->t;
     if (steps[i]) {
-      int rc = capture_window(hs[i], rs[i].window);
+      int rc = prepare_graphs(hs[i], rs[i].window);
       if (rc) return rc;
     }
   }
@@ -1255,35 +1302,6 @@ extern "C" int snn_get_stats(snn_handle h, snn_stats *out) {
   return SNN_OK;
 }
 
-// Capture `steps` steps of the two-kernel path on buffer set 0 into one graph,
-// with event record nodes around every kernel when `ev` is given.
-static int capture_timing_graph(snn_net *h, uint32_t steps, const L2Window &l2, cudaEvent_t *ev,
-                                cudaGraphExec_t *out) {
-  const NetDev d = descriptor(h, 0);
-  cudaStream_t cs = h->cap_stream;
-  CU_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  cudaError_t err = cudaSuccess;
-  for (uint32_t k = 0; k < steps && err == cudaSuccess; ++k) {
-    if (ev) err = cudaEventRecordWithFlags(ev[4 * k + 0], cs, cudaEventRecordExternal);
-    if (err == cudaSuccess) err = launch_update(d, k, h->cfg.update_block, h->cfg.update_groups, l2, cs);
-    if (ev && err == cudaSuccess) err = cudaEventRecordWithFlags(ev[4 * k + 1], cs, cudaEventRecordExternal);
-    if (ev && err == cudaSuccess) err = cudaEventRecordWithFlags(ev[4 * k + 2], cs, cudaEventRecordExternal);
-    if (err == cudaSuccess)
-      err = launch_deliver(d, k, (uint32_t)h->cfg.deliver_lanes, h->cfg.deliver_warps, deliver_grid(h), l2, cs);
-    if (ev && err == cudaSuccess) err = cudaEventRecordWithFlags(ev[4 * k + 3], cs, cudaEventRecordExternal);
-  }
-  cudaGraph_t g = nullptr;
-  cudaError_t e2 = cudaStreamEndCapture(cs, &g);
-  if (err != cudaSuccess || e2 != cudaSuccess) {
-    if (g) cudaGraphDestroy(g);
-    return fail(SNN_ERR_CUDA, std::string("timing graph capture: ") + cudaGetErrorString(err != cudaSuccess ? err : e2));
-  }
-  cudaError_t e3 = cudaGraphInstantiate(out, g, 0);
-  cudaGraphDestroy(g);
-  if (e3 != cudaSuccess) return fail(SNN_ERR_CUDA, std::string("timing graph instantiate: ") + cudaGetErrorString(e3));
-  return SNN_OK;
-}
-
 extern "C" int snn_time_kernels(snn_handle h, uint32_t steps, double *ms_out) {
   if (!h || !ms_out) return fail(SNN_ERR_ARG, "null argument");
   if (h->broken) return fail(SNN_ERR_STATE, "network is invalid after an earlier failure");
@@ -1313,11 +1331,13 @@ extern "C" int snn_time_kernels(snn_handle h, uint32_t steps, double *ms_out) {
     }
   } guard{&ev};
   guard.s = s;
-  rc = capture_timing_graph(h, steps, l2, nullptr, &guard.gx[0]);
+  const uint32_t phase = (uint32_t)(t0 % L.kmin);
+  uint32_t kernels = 0;
+  rc = capture_steps(h, descriptor(h, 0), steps, phase, l2, nullptr, &guard.gx[0], &kernels);
   if (rc) return rc;
-  rc = capture_timing_graph(h, steps, l2, ev.data(), &guard.gx[1]);
+  rc = capture_steps(h, descriptor(h, 0), steps, phase, l2, ev.data(), &guard.gx[1], nullptr);
   if (rc) return rc;
-  rc = dev_alloc(guard.snap, L.off_rows);   // V, c, ref, ring
+  rc = dev_alloc(guard.snap, L.off_rows);   // V, c, ref, input buffers, spike history
   if (rc) return rc;
   h->pinned_win->t0 = (uint32_t)t0;
   h->pinned_win->t_end = (uint32_t)(t0 + steps);
@@ -1335,22 +1355,26 @@ extern "C" int snn_time_kernels(snn_handle h, uint32_t steps, double *ms_out) {
   CU_TRY(cudaMemsetAsync(base + L.off_rec[0], 0, L.rec_block, s));
   // (2) the same steps with event nodes around every kernel; these results stay
   CU_TRY(cudaGraphLaunch(guard.gx[1], s));
-  h->launches += 4ull * steps;
+  h->launches += 2ull * kernels;
   rc = drain_window(h, 0, t0, s);
   if (rc) return rc;
   h->t = t0 + steps;
   double up = 0, dl = 0;
+  uint32_t n_dl = 0;
   for (uint32_t k = 0; k < steps; ++k) {
     float x = 0, y = 0;
     CU_TRY(cudaEventElapsedTime(&x, ev[4 * k + 0], ev[4 * k + 1]));
-    CU_TRY(cudaEventElapsedTime(&y, ev[4 * k + 2], ev[4 * k + 3]));
     up += x;
-    dl += y;
+    if ((phase + k + 1u) % L.kmin == 0u) {
+      CU_TRY(cudaEventElapsedTime(&y, ev[4 * k + 2], ev[4 * k + 3]));
+      dl += y;
+      ++n_dl;
+    }
   }
   float whole = 0;
   CU_TRY(cudaEventElapsedTime(&whole, a, b));
   ms_out[0] = up / steps;
-  ms_out[1] = dl / steps;
+  ms_out[1] = n_dl ? dl / n_dl : 0.0;
   ms_out[2] = (double)whole / steps;
   return SNN_OK;
 }

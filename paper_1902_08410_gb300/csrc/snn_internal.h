@@ -43,7 +43,7 @@ struct alignas(16) NetDev {
   uint32_t G, gx;       // modules, grid width
   uint32_t M;           // out-degree
   uint32_t M_pad;       // padded to a multiple of 8
-  uint32_t D;           // history slots = n_delay + 1
+  uint32_t D;           // spike-history slots = n_delay + kmin
   uint32_t fmt;         // 0 = f32 weights, 1 = i16 weights
   uint32_t row_bytes;   // bytes of one row: M_pad keys then M_pad weights
   uint32_t bin_steps;
@@ -51,9 +51,11 @@ struct alignas(16) NetDev {
   uint32_t slot;        // index of this network in a batch
   uint32_t rec_cap;     // raster entries per window
   uint32_t rates_bins;  // bins in the rate window
-  uint32_t n_delay;     // largest delay in steps (D - 1)
+  uint32_t n_delay;     // largest delay in steps
   uint32_t os;          // u16 entries per row of the delay-group table (multiple of 8)
-  uint32_t pad1[3];
+  uint32_t kmin;        // smallest delay: steps per exchange period (delivery after steps t with (t + 1) % kmin == 0)
+  uint32_t nbuf;        // input buffers = kmin + 1 (the input of step t is buffer t % nbuf)
+  uint32_t pad1;
 
   // --- per population constants (Eq. 2 propagators, Table S1)
   float pvv[kNPop], pvc[kNPop], pcc[kNPop];
@@ -66,13 +68,14 @@ struct alignas(16) NetDev {
   float *V;             // [N_pad]
   float *c;             // [N_pad]
   uint8_t *ref;         // [N_pad]
-  // Synaptic input of step t (2^-16 mV) = acc_loc[t & 1][n] + acc_rem[t & 1][n].
+  // Synaptic input of step t (2^-16 mV) = acc_loc[t % nbuf][n] + acc_rem[t % nbuf][n].
   // acc_loc holds what neurons receive from sources of their own module; the
-  // delivery writes it with plain stores (every entry, every step).  acc_rem
-  // receives reductions from other modules' sources (and, on the fused path,
-  // the delay-1 records of the step's own spikes); the update clears it.
-  int32_t *acc_loc;     // [2][N_pad]
-  int32_t *acc_rem;     // [2][N_pad]
+  // delivery writes it with plain stores (every entry, for every step).
+  // acc_rem receives reductions from other modules' sources (and, on the fused
+  // path, the delay-kmin records of the delivering step's own spikes); the
+  // update clears it.
+  int32_t *acc_loc;     // [nbuf][N_pad]
+  int32_t *acc_rem;     // [nbuf][N_pad]
   uint32_t *hcnt;       // [D][G] spikes of module m at a step with slot t mod D
   uint32_t *hist;       // [D][N] their ids: slot s, module m at s * N + m * 1250
   uint8_t *rows;        // [N][row_bytes]
@@ -91,7 +94,8 @@ struct BuildDev {
   const float *ztab;    // [kZTab]
   float J[kNPop][kNPop];
   float sig[kNPop][kNPop];
-  uint32_t n_delay;
+  uint32_t n_delay;     // delays uniform on min_delay..n_delay
+  uint32_t min_delay;
   int32_t p_local_mode; // 1 when p_local >= 0 (local bucket shortcut valid), 0 otherwise
 };
 

@@ -18,15 +18,17 @@
 //   reductions, so the sum does not depend on order).
 //
 // Delay-major delivery.  A row is stored grouped by delay (Sec. 2.1), with the
-// end of each delay group in a small table (offs).  At step t the delivery
-// adds, for d = 1..n_delay, the delay-d group of every spike of step
-// t + 1 - d, so every record handled at step t lands in the input of step
-// t + 1: the input is two int32 buffers per neuron (parity of t) instead of a
-// ring of n_delay + 1 slots.  The spikes of the last n_delay steps are kept
-// per (step slot, module) in `hist`.  A delivery block owns one module m at a
-// time: records of m's spikes whose target lies in m (80-100% of them) are
-// summed in shared memory and stored once per neuron (acc_loc); the others
-// are reduced into acc_rem.
+// end of each delay group in a small table (offs).  Delays run from kmin to
+// n_delay.  A delivery pass follows every kmin-th step t (the paper's exchange
+// step equals the minimum delay): it produces the inputs of steps t + 1 ..
+// t + kmin, for each of them adding, for d = kmin..n_delay, the delay-d group
+// of every spike of step T - d.  Every record handled lands in one of the
+// next kmin steps, so the input is kmin + 1 int32 buffers per neuron (the one
+// being read is never written) instead of a ring of n_delay + 1 slots.  The
+// spikes of the last n_delay + kmin steps are kept per (step slot, module) in
+// `hist`.  A delivery block owns one module m at a time: records of m's spikes
+// whose target lies in m (80-100% of them) are summed in shared memory and
+// stored once per neuron (acc_loc); the others are reduced into acc_rem.
 #include <algorithm>
 #include <cstdint>
 
@@ -261,19 +263,19 @@ __device__ __forceinline__ void load_state4(const NetDev &nd, uint32_t n0, Group
   g.ref = ld_na_u32(reinterpret_cast<const uint32_t *>(nd.ref) + i4);
 }
 
-// Input buffers of the step with parity `par`.  The remote buffer is cleared by
-// step4 after the neuron state is stored: a store right behind the load to the
-// same address held every later load of the warp back.
-__device__ __forceinline__ void load_input4(const NetDev &nd, uint32_t n0, uint32_t par, Group4 &g) {
-  const size_t o = (size_t)par * nd.N_pad;
+// Input buffers of the step (buffer `buf` = t % nbuf).  The remote buffer is
+// cleared by step4 after the neuron state is stored: a store right behind the
+// load to the same address held every later load of the warp back.
+__device__ __forceinline__ void load_input4(const NetDev &nd, uint32_t n0, uint32_t buf, Group4 &g) {
+  const size_t o = (size_t)buf * nd.N_pad;
   g.Il = ld_na_i4(reinterpret_cast<const int4 *>(nd.acc_loc + o) + (n0 >> 2));
   g.Ir = ld_na_i4(reinterpret_cast<const int4 *>(nd.acc_rem + o) + (n0 >> 2));
 }
 
-// Advance the 4 neurons of g by step t (input buffers of parity par, read by
+// Advance the 4 neurons of g by step t (input buffers `buf`, read by
 // load_input4); returns the 4-bit spike mask and adds the number of external
 // events to n_ext.
-__device__ __forceinline__ uint32_t step4(const NetDev &nd, uint32_t n0, uint32_t t, uint32_t par, Group4 &g,
+__device__ __forceinline__ uint32_t step4(const NetDev &nd, uint32_t n0, uint32_t t, uint32_t buf, Group4 &g,
                                           uint32_t &n_ext) {
   // one counter-based draw serves the four neurons (word n mod 4 each)
   const uint4 R = philox4x32_10(n0 >> 2, t, 1u, 0u, nd.key0, nd.key1);
@@ -309,7 +311,7 @@ __device__ __forceinline__ uint32_t step4(const NetDev &nd, uint32_t n0, uint32_
     reinterpret_cast<float4 *>(nd.V)[i4] = make_float4(Vv[0], Vv[1], Vv[2], Vv[3]);
     reinterpret_cast<float4 *>(nd.c)[i4] = make_float4(cv[0], cv[1], cv[2], cv[3]);
     reinterpret_cast<uint32_t *>(nd.ref)[i4] = rv[0] | (rv[1] << 8) | (rv[2] << 16) | (rv[3] << 24);
-    reinterpret_cast<int4 *>(nd.acc_rem + (size_t)par * nd.N_pad)[i4] = make_int4(0, 0, 0, 0);
+    reinterpret_cast<int4 *>(nd.acc_rem + (size_t)buf * nd.N_pad)[i4] = make_int4(0, 0, 0, 0);
   }
   return mask;
 }
@@ -317,9 +319,9 @@ __device__ __forceinline__ uint32_t step4(const NetDev &nd, uint32_t n0, uint32_
 __device__ __forceinline__ uint32_t update4(const NetDev &nd, uint32_t n0, uint32_t t, uint32_t &n_ext) {
   Group4 g;
   load_state4(nd, n0, g);
-  const uint32_t par = t & 1u;
-  load_input4(nd, n0, par, g);
-  return step4(nd, n0, t, par, g, n_ext);
+  const uint32_t buf = t % nd.nbuf;
+  load_input4(nd, n0, buf, g);
+  return step4(nd, n0, t, buf, g, n_ext);
 }
 
 // Warp-level recording of the warp's spikes over G groups (all 32 lanes
@@ -423,9 +425,12 @@ __device__ __forceinline__ void record_warp(const NetDev &nd, const uint32_t (&m
 }
 
 // ---------------------------------------------------------------------------
-// Delay-major delivery of one module (Sec. 2.1.1): for d = d_first..n_delay,
-// the delay-d records of the module's spikes of step t + 1 - d, all of which
-// land in the input of step t + 1.
+// Delay-major delivery of one module (Sec. 2.1.1).  A delivery pass follows
+// the update of every step t with (t + 1) % kmin == 0 (kmin = the smallest
+// delay: the spikes of kmin consecutive steps are delivered together, the
+// paper's exchange step equal to the minimum delay).  It produces the inputs
+// of the next kmin steps T = t + 1 .. t + kmin: for each T and each delay d in
+// kmin..n_delay, the delay-d records of the module's spikes of step T - d.
 // ---------------------------------------------------------------------------
 constexpr uint32_t kSegCap = 512;   // (spike, delay) segments described per pass
 
@@ -436,9 +441,8 @@ struct alignas(16) DeliverShared {
   uint32_t rng[kSegCap];      // its records [lo, hi): lo | hi << 16
 };
 
-__device__ __forceinline__ uint32_t slot_back(uint32_t tm, uint32_t d, uint32_t D) {
-  return (tm + 1u + D - d) % D;   // slot of step t + 1 - d, tm = t mod D, 1 <= d < D
-}
+// Slot of step T - d, Tm = T mod D, 1 <= d < D.
+__device__ __forceinline__ uint32_t slot_back(uint32_t Tm, uint32_t d, uint32_t D) { return (Tm + D - d) % D; }
 
 // Add the records [a, b) of source s's row: targets inside the module
 // [mbase, mbase + 1250) into shared memory, the others into `rem`.
@@ -473,107 +477,115 @@ __device__ __forceinline__ void add_records(const NetDev &nd, DeliverShared &sh,
   }
 }
 
-// Block-wide (every thread calls it with the same arguments).  sh.acc is zero
-// on entry and on return.
-__device__ __forceinline__ void deliver_module(const NetDev &nd, DeliverShared &sh, uint32_t t, uint32_t m, uint32_t d_first,
-                               uint32_t lanes) {
-  const uint32_t tid = threadIdx.x, nthr = blockDim.x;
-  const uint32_t D = nd.D, nd_max = nd.n_delay, tm = t % D;
-  const uint32_t par1 = (t + 1u) & 1u;
-  const uint32_t mbase = m * (uint32_t)kK;
-  // 1. segments per delay and their prefix sums (one warp; n_delay <= 254)
-  if (tid < 32u) {
-    uint32_t v[8], sum = 0;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const uint32_t d = tid * 8u + 1u + (uint32_t)i;
-      v[i] = (d >= d_first && d <= nd_max) ? nd.hcnt[(size_t)slot_back(tm, d, D) * nd.G + m] : 0u;
-      sum += v[i];
-    }
-    uint32_t incl = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-      if (tid >= (uint32_t)o) incl += y;
-    }
-    uint32_t acc = incl - sum;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      acc += v[i];
-      sh.pre[tid * 8u + 1u + (uint32_t)i] = acc;
-    }
-    if (tid == 0) sh.pre[0] = 0u;
-  }
-  __syncthreads();
-  const uint32_t S = sh.pre[nd_max];
-  int32_t *rem = nd.acc_rem + (size_t)par1 * nd.N_pad;
-  const uint32_t grp = tid / lanes, sub = tid % lanes, ngrp = nthr / lanes;
+// Prefetch into L2 the next delay group (after record b) of source s's row.
+__device__ __forceinline__ void prefetch_next_group(const NetDev &nd, uint32_t s, const uint16_t *o, uint32_t d,
+                                                    uint32_t b) {
+  if (d >= nd.n_delay) return;
+  const uint32_t c2 = o[d + 1u];
+  if (c2 <= b) return;
   const uint32_t wb = nd.fmt ? 2u : 4u;
-  for (uint32_t p0 = 0; p0 < S; p0 += kSegCap) {
-    const uint32_t np = min(kSegCap, S - p0);
-    // 2. describe the pass's segments: source, and its delay-d records
-    for (uint32_t j = tid; j < np; j += nthr) {
-      const uint32_t kseg = p0 + j;
-      uint32_t lo = 1u, hi = nd_max;   // smallest d with pre[d] > kseg
-      while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (sh.pre[mid] > kseg) hi = mid; else lo = mid + 1u;
+  const uint8_t *row = nd.rows + (size_t)s * nd.row_bytes;
+  prefetch_range_l2(row + (size_t)b * 4u, (c2 - b) * 4u);
+  prefetch_range_l2(row + (size_t)nd.M_pad * 4u + (size_t)b * wb, (c2 - b) * wb);
+}
+
+// The delivery pass after step t for module m.  With skip_current the spikes
+// of step t are left out (the fused step delivers them from the blocks that
+// produced them, whose lists are complete before the module's history is).
+// Block-wide (every thread calls it with the same arguments); sh.acc is zero
+// on entry and on return.
+__device__ __forceinline__ void deliver_module(const NetDev &nd, DeliverShared &sh, uint32_t t, uint32_t m,
+                                               bool skip_current, uint32_t lanes) {
+  const uint32_t tid = threadIdx.x, nthr = blockDim.x;
+  const uint32_t D = nd.D, dmax = nd.n_delay, kmin = nd.kmin;
+  const uint32_t mbase = m * (uint32_t)kK;
+  const uint32_t grp = tid / lanes, sub = tid % lanes, ngrp = nthr / lanes;
+  for (uint32_t j = 0; j < kmin; ++j) {
+    const uint32_t T = t + 1u + j, Tm = T % D;   // target step
+    const uint32_t buf = T % nd.nbuf;
+    // 1. segments per delay and their prefix sums (one warp; n_delay <= 254)
+    if (tid < 32u) {
+      uint32_t v[8], sum = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const uint32_t d = tid * 8u + 1u + (uint32_t)i;
+        const bool use = d >= kmin && d <= dmax && !(skip_current && d == j + 1u);
+        v[i] = use ? nd.hcnt[(size_t)slot_back(Tm, d, D) * nd.G + m] : 0u;
+        sum += v[i];
       }
-      const uint32_t d = lo, i = kseg - sh.pre[d - 1u];
-      const uint32_t s = nd.hist[(size_t)slot_back(tm, d, D) * nd.N + mbase + i];
-      const uint16_t *o = nd.offs + (size_t)s * nd.os;
-      const uint32_t a = o[d - 1u], b = o[d];
-      sh.src[j] = s;
-      sh.rng[j] = a | (b << 16);
-      if (d < nd_max) {   // this spike's next delay group is read at the next step
-        const uint32_t c2 = o[d + 1u];
-        if (c2 > b) {
-          const uint8_t *row = nd.rows + (size_t)s * nd.row_bytes;
-          prefetch_range_l2(row + (size_t)b * 4u, (c2 - b) * 4u);
-          prefetch_range_l2(row + (size_t)nd.M_pad * 4u + (size_t)b * wb, (c2 - b) * wb);
-        }
+      uint32_t incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (tid >= (uint32_t)o) incl += y;
       }
+      uint32_t acc = incl - sum;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        acc += v[i];
+        sh.pre[tid * 8u + 1u + (uint32_t)i] = acc;
+      }
+      if (tid == 0) sh.pre[0] = 0u;
     }
     __syncthreads();
-    // 3. their records, `lanes` lanes per segment
-    for (uint32_t j = grp; j < np; j += ngrp)
-      add_records(nd, sh, rem, sh.src[j], sh.rng[j] & 0xFFFFu, sh.rng[j] >> 16, sub, lanes, mbase);
+    const uint32_t S = sh.pre[dmax];
+    int32_t *rem = nd.acc_rem + (size_t)buf * nd.N_pad;
+    for (uint32_t p0 = 0; p0 < S; p0 += kSegCap) {
+      const uint32_t np = min(kSegCap, S - p0);
+      // 2. describe the pass's segments: source, and its delay-d records
+      for (uint32_t q = tid; q < np; q += nthr) {
+        const uint32_t kseg = p0 + q;
+        uint32_t lo = 1u, hi = dmax;   // smallest d with pre[d] > kseg
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (sh.pre[mid] > kseg) hi = mid; else lo = mid + 1u;
+        }
+        const uint32_t d = lo, i = kseg - sh.pre[d - 1u];
+        const uint32_t s = nd.hist[(size_t)slot_back(Tm, d, D) * nd.N + mbase + i];
+        const uint16_t *o = nd.offs + (size_t)s * nd.os;
+        const uint32_t a = o[d - 1u], b = o[d];
+        sh.src[q] = s;
+        sh.rng[q] = a | (b << 16);
+        prefetch_next_group(nd, s, o, d, b);   // read at a later step
+      }
+      __syncthreads();
+      // 3. their records, `lanes` lanes per segment
+      for (uint32_t q = grp; q < np; q += ngrp)
+        add_records(nd, sh, rem, sh.src[q], sh.rng[q] & 0xFFFFu, sh.rng[q] >> 16, sub, lanes, mbase);
+      __syncthreads();
+    }
+    // 4. the module's own input of step T: one plain store per neuron
+    int2 *dst = reinterpret_cast<int2 *>(nd.acc_loc + (size_t)buf * nd.N_pad + mbase);
+    int2 *src = reinterpret_cast<int2 *>(sh.acc);
+    for (uint32_t i = tid; i < (uint32_t)kK / 2u; i += nthr) {
+      dst[i] = src[i];
+      src[i] = make_int2(0, 0);
+    }
     __syncthreads();
   }
-  // 4. the module's own input of step t + 1: one plain store per neuron
-  int2 *dst = reinterpret_cast<int2 *>(nd.acc_loc + (size_t)par1 * nd.N_pad + mbase);
-  int2 *src = reinterpret_cast<int2 *>(sh.acc);
-  for (uint32_t i = tid; i < (uint32_t)kK / 2u; i += nthr) {
-    dst[i] = src[i];
-    src[i] = make_int2(0, 0);
-  }
-  if (tid == 0) nd.hcnt[(size_t)((tm + 1u) % D) * nd.G + m] = 0u;   // the slot step t + 1 appends to
+  // the slots the next kmin steps append to (none of them read above)
+  for (uint32_t i = tid; i < kmin; i += nthr) nd.hcnt[(size_t)((t + 1u + i) % D) * nd.G + m] = 0u;
   __syncthreads();
 }
 
-// Fused step: the delay-1 records of the block's own spikes of step t,
-// reduced straight into the remote buffer of step t + 1 (the module's history
-// of step t is not complete while other blocks still update its neurons).
-__device__ void deliver_own_delay1(const NetDev &nd, const uint32_t *ids, uint32_t cnt, uint32_t t, uint32_t lanes) {
+// Fused step, delivery pass after step t: the delay-kmin records of the
+// block's own spikes of step t, reduced straight into the remote buffer of
+// step t + kmin (the module's history of step t is not complete while other
+// blocks still update its neurons).
+__device__ void deliver_own(const NetDev &nd, const uint32_t *ids, uint32_t cnt, uint32_t t, uint32_t lanes) {
   const uint32_t tid = threadIdx.x;
   const uint32_t grp = tid / lanes, sub = tid % lanes, ngrp = blockDim.x / lanes;
-  int32_t *rem = nd.acc_rem + (size_t)((t + 1u) & 1u) * nd.N_pad;
-  const uint32_t wb = nd.fmt ? 2u : 4u;
+  const uint32_t kmin = nd.kmin;
+  int32_t *rem = nd.acc_rem + (size_t)((t + kmin) % nd.nbuf) * nd.N_pad;
   for (uint32_t j = grp; j < cnt; j += ngrp) {
     const uint32_t s = ids[j];
     const uint16_t *o = nd.offs + (size_t)s * nd.os;
-    const uint32_t b = o[1];
+    const uint32_t a = o[kmin - 1u], b = o[kmin];
     const uint8_t *row = nd.rows + (size_t)s * nd.row_bytes;
     const uint32_t *keys = reinterpret_cast<const uint32_t *>(row);
     const uint8_t *wrow = row + (size_t)nd.M_pad * 4u;
-    if (sub == 0 && nd.n_delay > 1u) {
-      const uint32_t c2 = o[2];
-      if (c2 > b) {
-        prefetch_range_l2(row + (size_t)b * 4u, (c2 - b) * 4u);
-        prefetch_range_l2(wrow + (size_t)b * wb, (c2 - b) * wb);
-      }
-    }
-    for (uint32_t r = sub; r < b; r += lanes) {
+    if (sub == 0) prefetch_next_group(nd, s, o, kmin, b);
+    for (uint32_t r = a + sub; r < b; r += lanes) {
       const uint32_t key = ld_rec_u32(keys + r);
       const int32_t v = nd.fmt ? ld_rec_s16(reinterpret_cast<const int16_t *>(wrow) + r) * 64
                                : __float2int_rn(__fmul_rn(ld_rec_f32(reinterpret_cast<const float *>(wrow) + r),
@@ -691,7 +703,7 @@ __global__ void __launch_bounds__(kBuildWarpsMax * 32) k_build_rows(const __grid
       }
       const uint32_t lt = __umulhi(r.y, (uint32_t)kK);
       const uint32_t tgt = mt * (uint32_t)kK + lt;
-      const uint32_t d = 1u + __umulhi(r.z, nd_del);
+      const uint32_t d = bd.min_delay + __umulhi(r.z, nd_del - bd.min_delay + 1u);
       w_key[j] = (d << 24) | tgt;
       w_z[j] = (uint16_t)(r.w >> 20);
     }
@@ -826,16 +838,16 @@ __global__ void __launch_bounds__(BLOCK, G == 1 ? 1280 / BLOCK : 1) k_update(con
   const NetWin w = *nd.win;
   const uint32_t t = w.t0 + k;
   if (t >= w.t_end) return;
-  const uint32_t par = t & 1u;
+  const uint32_t buf = t % nd.nbuf;
 #pragma unroll
   for (int g = 0; g < G; ++g)
-    if (live[g]) load_input4(nd, n0[g], par, st4[g]);
+    if (live[g]) load_input4(nd, n0[g], buf, st4[g]);
   uint32_t mask[G], n_ext[G];
 #pragma unroll
   for (int g = 0; g < G; ++g) {
     mask[g] = 0;
     n_ext[g] = 0;
-    if (live[g]) mask[g] = step4(nd, n0[g], t, par, st4[g], n_ext[g]);
+    if (live[g]) mask[g] = step4(nd, n0[g], t, buf, st4[g], n_ext[g]);
   }
   // record per group whose tile is live (warp-uniform)
   if (live[G - 1]) {
@@ -852,28 +864,29 @@ __global__ void __launch_bounds__(BLOCK, G == 1 ? 1280 / BLOCK : 1) k_update(con
 }
 
 // ---------------------------------------------------------------------------
-// Kernel: delivery of step t (two-kernel path), every delay including 1 (the
-// update kernel of step t has completed its module histories).  Blocks take
-// modules m = blockIdx.x, blockIdx.x + gridDim.x, ...
+// Kernel: delivery pass after step t (two-kernel path; the update kernel of
+// step t has completed the module histories).  Blocks take modules
+// m = blockIdx.x, blockIdx.x + gridDim.x, ...
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256, 4) k_deliver(const __grid_constant__ NetDev nd, uint32_t k, uint32_t lanes) {
   __shared__ DeliverShared sh;
   const NetWin w = *nd.win;
   const uint32_t t = w.t0 + k;
-  if (t >= w.t_end) return;
+  if (t >= w.t_end || (t + 1u) % nd.kmin != 0u) return;   // launched after the last step of an exchange period
   for (uint32_t i = threadIdx.x; i < (uint32_t)kK + 2u; i += blockDim.x) sh.acc[i] = 0;
   __syncthreads();
-  for (uint32_t m = blockIdx.x; m < nd.G; m += gridDim.x) deliver_module(nd, sh, t, m, 1u, lanes);
+  for (uint32_t m = blockIdx.x; m < nd.G; m += gridDim.x) deliver_module(nd, sh, t, m, false, lanes);
 }
 
 // ---------------------------------------------------------------------------
 // Kernel: fused step over a table of networks.  A block takes work items
 // (network, 4*blockDim neurons, range of modules): update and recording with a
-// block-local spike list, the delay-1 records of those spikes, then the
-// delay >= 2 input of the item's modules.  Update reads the input buffers of
-// parity t and delivery writes those of parity t + 1, so blocks need no
-// grid-wide barrier; many small blocks per SM let one block's update overlap
-// another's delivery.  Launched with programmatic dependent launch: the
+// block-local spike list and, after the last step of an exchange period, the
+// delay-kmin records of those spikes and the rest of the item's modules'
+// input for the next kmin steps.  Update reads input buffer t % nbuf and
+// delivery writes the buffers of steps t + 1 .. t + kmin (nbuf = kmin + 1:
+// never the one being read), so blocks need no grid-wide barrier; many small
+// blocks per SM let one block's update overlap another's delivery.  Launched with programmatic dependent launch: the
 // prologue (descriptor copy, window read) runs while the previous step drains.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(512) k_fused(const __grid_constant__ FusedTable tab, uint32_t k) {
@@ -917,8 +930,10 @@ __global__ void __launch_bounds__(512) k_fused(const __grid_constant__ FusedTabl
       record_warp<1>(nd, mask, a1, n_ext, t, k, s_win.bin0, s_ids, &s_count);
     }
     __syncthreads();
-    deliver_own_delay1(nd, s_ids, s_count, t, tab.lanes);
-    for (uint32_t m = item.m_begin; m < item.m_end; ++m) deliver_module(nd, sh, t, m, 2u, tab.lanes);
+    if ((t + 1u) % nd.kmin == 0u) {   // the last step of an exchange period: delivery pass
+      deliver_own(nd, s_ids, s_count, t, tab.lanes);
+      for (uint32_t m = item.m_begin; m < item.m_end; ++m) deliver_module(nd, sh, t, m, true, tab.lanes);
+    }
   }
   if (!waited) {
     pdl_wait();

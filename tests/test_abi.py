@@ -54,6 +54,7 @@ def test_footprint_host_only(snn):
 @pytest.mark.parametrize("field,value,code", [
     ("gx", 0, -1), ("lambda", 0.0, -1), ("n_delay", 0, -1), ("n_delay", 300, -1),
     ("record_format", 7, -1), ("out_degree", 5000, -6), ("gx", 120, -6), ("bin_steps", 0, -1),
+    ("min_delay", 21, -1), ("min_delay", -1, -1),
 ])
 def test_invalid_parameters_rejected(snn, field, value, code):
     p = W.base_params(2, 2, 1.0)

@@ -347,6 +347,27 @@ def test_delay_target_weight_laws(oracle_mod):
         assert np.all(np.sign(w[w != 0]) == np.sign(J))
 
 
+@pytest.mark.parametrize("min_delay,n_delay", [(10, 20), (20, 20), (3, 254)])
+def test_min_delay_law(oracle_mod, min_delay, n_delay):
+    """Delays uniform on min_delay..n_delay (the paper's 1 ms minimum delay,
+    Sec. 2.1.1, is 10 steps of 0.1 ms); min_delay 0 and 1 give the same rows."""
+    p = W.base_params(3, 3, 1.0)
+    p["n_delay"], p["min_delay"] = n_delay, min_delay
+    net = oracle_mod.OracleNet(p, 5)
+    keys, _ = net.rows(range(4 * W.K, 4 * W.K + 1250, 5))
+    d = (keys >> 24).ravel()
+    span = n_delay - min_delay + 1
+    assert d.min() >= min_delay and d.max() <= n_delay
+    if span > 1:
+        assert d.min() == min_delay and d.max() == n_delay
+        counts = np.bincount(d - min_delay, minlength=span)
+        assert _chi2_p(counts, np.full(span, d.size / span)) > 1e-3
+    p0, p1 = dict(p), dict(p)
+    p0["min_delay"], p1["min_delay"] = 0, 1
+    a, b = oracle_mod.OracleNet(p0, 5), oracle_mod.OracleNet(p1, 5)
+    assert np.array_equal(a.row(7000)[0], b.row(7000)[0])
+
+
 def test_rows_are_stable_sorted_by_delay_then_target(oracle_mod):
     """Rows hold the individually drawn synapses ordered by delay, then target,
     then draw index (NumPy's lexicographic sort of the drawn records)."""
@@ -398,11 +419,12 @@ def _wfix(w, fmt):
     return np.rint(w * np.float32(65536.0)).astype(np.int64)
 
 
-@pytest.mark.parametrize("fmt", [W.REC_F32, W.REC_I16])
-def test_recurrent_input_definition(oracle_mod, fmt):
+@pytest.mark.parametrize("fmt,min_delay", [(W.REC_F32, 1), (W.REC_I16, 1), (W.REC_F32, 10)])
+def test_recurrent_input_definition(oracle_mod, fmt, min_delay):
     """Input read at step t = sum over spikes (t', s) and records (d, tgt) of s
     with t' + d = t of the record's fixed-point weight."""
     p = W.base_params(2, 1, 1.0, "AW", record_format=fmt)
+    p["min_delay"] = min_delay
     net = oracle_mod.OracleNet(p, 21)
     T = 400
     net.enable_trace(0, T)

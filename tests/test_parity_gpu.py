@@ -156,6 +156,38 @@ def test_delay_range_bins_and_time_step(snn, oracle_mod, n_delay, bin_steps, dt_
         g.close()
 
 
+@pytest.mark.parametrize("n_delay,min_delay", [(20, 10), (7, 4), (20, 20)])
+def test_min_delay_exchange_periods(snn, oracle_mod, n_delay, min_delay):
+    """Delays on min_delay..n_delay: the spikes of min_delay consecutive steps
+    are delivered in one pass after the last of them (Sec. 2.1.1; the paper's
+    exchange step of 1 ms = 10 steps).  Both launch paths, both record formats,
+    runs and windows that start at every phase of an exchange period."""
+    for fmt in (W.REC_F32, W.REC_I16):
+        p = W.base_params(2, 3, 0.6, "AW", record_format=fmt)
+        p["n_delay"], p["min_delay"] = n_delay, min_delay
+        o = _oracle(oracle_mod, p, 41, 700)
+        assert o.counters()["spikes"] > 1000
+        for path, window in ((0, 33), (0, 351), (1, 64)):
+            g = snn.Network(p, 41)
+            g.launch = {"path": path, "window_steps": window}
+            for n in (3, 401, 96, 200):
+                g.run(n)
+            _assert_same_run(g, o, 700)
+            g.close()
+    # the tuner and the kernel timing keep results at a minimum delay too
+    p = W.base_params(2, 3, 0.6, "AW")
+    p["n_delay"], p["min_delay"] = n_delay, min_delay
+    o = _oracle(oracle_mod, p, 41, 700)
+    g = snn.Network(p, 41)
+    g.run(203)
+    g.autotune(30)
+    tk = g.time_kernels(97)
+    assert tk["update_ms"] > 0 and tk["deliver_ms"] > 0
+    g.run(400)
+    _assert_same_run(g, o, 700)
+    g.close()
+
+
 def test_run_table_s1_pure_kernel(snn, oracle_mod):
     """Table S1 three-population efficacies with the pure Eq. 1 kernel."""
     p = W.table_s1_params(3, 3, 0.6, "AW_8.8Hz")

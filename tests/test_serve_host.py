@@ -13,7 +13,7 @@ class FakeNet:
     peak = 0
     log = []
 
-    def __init__(self, params, seed):
+    def __init__(self, params, seed, stream=None):
         self.params, self.seed = params, seed
         self.N = params["n"]
         self.M = 3
@@ -49,6 +49,7 @@ def fakes(monkeypatch):
     monkeypatch.setattr(serve, "Network", FakeNet)
     monkeypatch.setattr(serve, "run_batch", fake_run_batch)
     monkeypatch.setattr(serve, "footprint", lambda p: p["bytes"])
+    monkeypatch.setattr(serve, "_own_stream", lambda: None)
     return FakeNet
 
 
@@ -76,13 +77,34 @@ def test_admission_by_footprint_in_arrival_order(fakes):
 
 
 def test_later_arrivals_join_between_chunks(fakes):
-    srv = serve.Server(memory_budget=1000, chunk_steps=10, realtime=False)
+    # builds on the calling thread: join times are exact on the chunk clock
+    srv = serve.Server(memory_budget=1000, chunk_steps=10, realtime=False, overlap=False)
     srv.submit({"n": 10, "bytes": 1}, seed=0, steps=50, arrival_s=0.0)
     srv.submit({"n": 10, "bytes": 1}, seed=1, steps=10, arrival_s=2.0)   # arrives after two chunks
     out = srv.run()
     r0, r1 = out["results"]
     assert r1.admitted_s >= 2.0 and r1.completed_s < r0.completed_s     # joined the running batch
     assert fakes.peak == 2
+
+
+@pytest.mark.parametrize("overlap", [True, False])
+def test_overlap_keeps_order_ledger_and_results(fakes, overlap):
+    """With the helper thread (builds and releases off the main thread) and
+    without it, admission stays in arrival order, the ledger never exceeds the
+    budget and every request advances exactly its steps."""
+    srv = serve.Server(memory_budget=70, chunk_steps=7, realtime=False, overlap=overlap)
+    sizes = [30, 30, 30, 20, 50, 10]
+    for i, b in enumerate(sizes):
+        srv.submit({"n": 10, "bytes": b}, seed=i, steps=11 + 3 * i, arrival_s=float(i % 3))
+    out = srv.run()
+    assert [r.stats["t"] for r in out["results"]] == [11 + 3 * i for i in range(6)]
+    arrival_order = sorted(range(6), key=lambda i: (i % 3, i))
+    assert [s for ev, s in fakes.log if ev == "admit"] == arrival_order
+    used = 0
+    for ev, s in fakes.log:
+        used += sizes[s] if ev == "admit" else -sizes[s]
+        assert used <= 70
+    assert fakes.live == 0
 
 
 def test_request_larger_than_budget(fakes):

@@ -89,7 +89,7 @@ def base_params(gx: int, gy: int, lam: float, regime: str = "SWA",
     reg = REGIMES[regime]
     p = {
         "gx": int(gx), "gy": int(gy), "lambda": float(lam), "p_local": float(p_local),
-        "out_degree": OUT_DEGREE, "n_delay": N_DELAY, "dt_ms": DT_MS,
+        "out_degree": OUT_DEGREE, "n_delay": N_DELAY, "min_delay": 1, "dt_ms": DT_MS,
         "record_format": int(record_format), "bin_steps": BIN_STEPS,
         "dJ_frac": 0.25, "dJ_ext_frac": 0.25,
         "J": [[J_EXC, J_EXC, J_INH] for _ in range(3)],
