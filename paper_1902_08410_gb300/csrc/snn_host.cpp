@@ -258,15 +258,15 @@ void build_inputs(const snn_params &p, BuildDev &bd) {
 // ---------------------------------------------------------------------------
 // network object
 // ---------------------------------------------------------------------------
-// Device arena of one network, in this order: V, c, ref, the input buffers
-// acc_loc[2] and acc_rem[2], the per-module spike counts and spike history of
-// the last n_delay + 1 steps (everything a run modifies), synapse rows, their
+// Device arena of one network, in this order: V, c, ref, the input buffers of
+// the next min_delay + 1 steps, the spike counts and spike lists of the last
+// n_delay + min_delay steps (everything a run modifies), synapse rows, their
 // delay-group table, amplitude table, two windows, two recording blocks
 // (header, external-event slots, rate window: one contiguous copy per window),
 // two raster entry buffers.  Windows alternate between the two buffer sets, so
 // the host drains one window's records while the GPU runs the next.
 struct Layout {
-  size_t off_V, off_c, off_ref, off_acc_loc, off_acc_rem, off_hcnt, off_hist, off_rows, off_offs, off_amp;
+  size_t off_V, off_c, off_ref, off_acc, off_cnt, off_hist, off_rows, off_offs, off_amp;
   size_t off_win[2], off_rec[2], off_ext[2], off_rates[2], off_entries[2];
   size_t rec_block;   // bytes of one recording block
   size_t total;
@@ -336,10 +336,9 @@ static Layout make_layout(const snn_params &p) {
   L.off_V = take((size_t)L.N_pad * 4);
   L.off_c = take((size_t)L.N_pad * 4);
   L.off_ref = take((size_t)L.N_pad);
-  L.off_acc_loc = take((size_t)L.nbuf * L.N_pad * 4);
-  L.off_acc_rem = take((size_t)L.nbuf * L.N_pad * 4);
-  L.off_hcnt = take((size_t)L.D * L.G * 4);
-  L.off_hist = take((size_t)L.D * L.N * 4);
+  L.off_acc = take((size_t)L.nbuf * L.N_pad * 4);
+  L.off_cnt = take((size_t)L.D * 4);
+  L.off_hist = take((size_t)L.D * L.N_pad * 4);
   L.off_rows = take((size_t)L.N * L.row_bytes);
   L.off_offs = take((size_t)L.N * L.os * 2);
   L.off_amp = take((size_t)kNPop * kZTab * 4);
@@ -433,8 +432,8 @@ static void l2_release(snn_net *h) {
 
 // Bytes of the persisting window at the start of the arena: V, c, ref, the
 // input buffers and the spike counts when they fit the set-aside together,
-// else V, c and ref alone.  The spike history (sparse: only the ids of recent
-// spikes are touched) is never part of it.
+// else V, c and ref alone.  The spike lists (sparse: only the ids of recent
+// spikes are touched) are never part of it.
 static size_t l2_window_bytes(const snn_net *h) {
   int dev = 0, max_win = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -442,7 +441,7 @@ static size_t l2_window_bytes(const snn_net *h) {
     cudaGetLastError();
     return 0;
   }
-  const size_t all = h->L.off_hist, state = h->L.off_acc_loc;
+  const size_t all = h->L.off_hist, state = h->L.off_acc;
   return std::min<size_t>(all <= g_l2_setaside ? all : state, (size_t)max_win);
 }
 
@@ -563,9 +562,8 @@ static void fill_descriptor(snn_net *h) {
   d.V = reinterpret_cast<float *>(base + L.off_V);
   d.c = reinterpret_cast<float *>(base + L.off_c);
   d.ref = base + L.off_ref;
-  d.acc_loc = reinterpret_cast<int32_t *>(base + L.off_acc_loc);
-  d.acc_rem = reinterpret_cast<int32_t *>(base + L.off_acc_rem);
-  d.hcnt = reinterpret_cast<uint32_t *>(base + L.off_hcnt);
+  d.acc = reinterpret_cast<int32_t *>(base + L.off_acc);
+  d.cnt = reinterpret_cast<uint32_t *>(base + L.off_cnt);
   d.hist = reinterpret_cast<uint32_t *>(base + L.off_hist);
   d.rows = base + L.off_rows;
   d.offs = reinterpret_cast<const uint16_t *>(base + L.off_offs);
@@ -657,7 +655,7 @@ extern "C" int snn_build_network(const snn_params *p, uint64_t seed, void *cuda_
   h->launches += 2;
   bd.cdf = d_cdf;
   bd.ztab = d_z;
-  CU_TRY(cudaMemsetAsync(base + L.off_acc_loc, 0, L.off_hist - L.off_acc_loc, s));   // inputs, spike counts
+  CU_TRY(cudaMemsetAsync(base + L.off_acc, 0, L.off_hist - L.off_acc, s));   // inputs, spike counts
   CU_TRY(cudaMemsetAsync(base + L.off_win[0], 0, L.off_entries[0] - L.off_win[0], s));   // windows, blocks
   CU_TRY(cudaMallocHost(&h->pinned_win, 2 * sizeof(NetWin)));
   std::memset(h->pinned_win, 0, 2 * sizeof(NetWin));
@@ -1063,12 +1061,10 @@ static int run_fused(snn_net *const *hs, const uint64_t *steps, int32_t n) {
     if (hs[i]->stream != s) CU_TRY(cudaStreamSynchronize(hs[i]->stream));
   size_t it = 0;
   for (int i = 0; i < n; ++i) {
-    // items of network i: consecutive neuron ranges; its modules are spread
-    // evenly over them (item j delivers modules [j G / I, (j + 1) G / I))
-    const uint64_t I = (hs[i]->L.N_pad + npi - 1) / npi, G = hs[i]->L.G;
-    for (uint64_t j = 0; j < I; ++j)
-      B.pinned_items[it++] = FusedItem{(uint32_t)i, (uint32_t)(j * npi), (uint32_t)(j * G / I),
-                                       (uint32_t)((j + 1) * G / I)};
+    // items of network i: consecutive neuron ranges, each knowing its index
+    // among the network's items (its share of the network's delivery)
+    const uint32_t I = (hs[i]->L.N_pad + npi - 1) / npi;
+    for (uint32_t j = 0; j < I; ++j) B.pinned_items[it++] = FusedItem{(uint32_t)i, j * npi, j, I};
   }
   for (int b = 0; b < 2; ++b)
     for (int i = 0; i < n; ++i) {

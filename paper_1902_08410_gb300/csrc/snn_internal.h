@@ -68,16 +68,11 @@ struct alignas(16) NetDev {
   float *V;             // [N_pad]
   float *c;             // [N_pad]
   uint8_t *ref;         // [N_pad]
-  // Synaptic input of step t (2^-16 mV) = acc_loc[t % nbuf][n] + acc_rem[t % nbuf][n].
-  // acc_loc holds what neurons receive from sources of their own module; the
-  // delivery writes it with plain stores (every entry, for every step).
-  // acc_rem receives reductions from other modules' sources (and, on the fused
-  // path, the delay-kmin records of the delivering step's own spikes); the
-  // update clears it.
-  int32_t *acc_loc;     // [nbuf][N_pad]
-  int32_t *acc_rem;     // [nbuf][N_pad]
-  uint32_t *hcnt;       // [D][G] spikes of module m at a step with slot t mod D
-  uint32_t *hist;       // [D][N] their ids: slot s, module m at s * N + m * 1250
+  // Synaptic input of step t (2^-16 mV): acc[t % nbuf][n], accumulated by
+  // reductions during the delivery pass before step t, cleared by the update.
+  int32_t *acc;         // [nbuf][N_pad]
+  uint32_t *cnt;        // [D] spikes of the step with slot t mod D
+  uint32_t *hist;       // [D][N_pad] their ids, in the order they were appended
   uint8_t *rows;        // [N][row_bytes]
   const uint16_t *offs; // [N][os] delay groups: records with delay <= d end at offs[s * os + d]
   const int32_t *amp;   // [3][kZTab] external amplitudes, 2^-16 mV
@@ -100,12 +95,13 @@ struct BuildDev {
 };
 
 // Work item of the fused step kernel: a range of one network's neurons to
-// update, and a range of its modules whose delayed input (delays >= 2) to deliver.
+// update; the item's index among its network's items also selects its share
+// of the network's delivery work.
 struct FusedItem {
   uint32_t net;         // index into the NetDev table
   uint32_t n_begin;     // first neuron (multiple of 4)
-  uint32_t m_begin;     // first module delivered
-  uint32_t m_end;       // one past the last module delivered
+  uint32_t index;       // index of the item among its network's items
+  uint32_t count;       // items of the network
 };
 
 struct FusedTable {

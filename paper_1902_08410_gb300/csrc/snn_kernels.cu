@@ -24,11 +24,9 @@
 // t + kmin, for each of them adding, for d = kmin..n_delay, the delay-d group
 // of every spike of step T - d.  Every record handled lands in one of the
 // next kmin steps, so the input is kmin + 1 int32 buffers per neuron (the one
-// being read is never written) instead of a ring of n_delay + 1 slots.  The
-// spikes of the last n_delay + kmin steps are kept per (step slot, module) in
-// `hist`.  A delivery block owns one module m at a time: records of m's spikes
-// whose target lies in m (80-100% of them) are summed in shared memory and
-// stored once per neuron (acc_loc); the others are reduced into acc_rem.
+// being read is never written; they stay in L2) instead of a ring of
+// n_delay + 1 slots.  The spikes of the last n_delay + kmin steps are kept per
+// step slot in `hist`.
 #include <algorithm>
 #include <cstdint>
 
@@ -253,7 +251,7 @@ __device__ __forceinline__ bool neuron_step(const NetDev &nd, int pop, float &V,
 struct Group4 {
   float4 V, c;
   uint32_t ref;   // 4 x u8
-  int4 Il, Ir;    // input of the step from the module's own sources / from the others
+  int4 I;         // synaptic input of the step
 };
 
 __device__ __forceinline__ void load_state4(const NetDev &nd, uint32_t n0, Group4 &g) {
@@ -263,13 +261,11 @@ __device__ __forceinline__ void load_state4(const NetDev &nd, uint32_t n0, Group
   g.ref = ld_na_u32(reinterpret_cast<const uint32_t *>(nd.ref) + i4);
 }
 
-// Input buffers of the step (buffer `buf` = t % nbuf).  The remote buffer is
-// cleared by step4 after the neuron state is stored: a store right behind the
-// load to the same address held every later load of the warp back.
+// Input buffer of the step (buffer `buf` = t % nbuf).  It is cleared by step4
+// after the neuron state is stored: a store right behind the load to the same
+// address held every later load of the warp back.
 __device__ __forceinline__ void load_input4(const NetDev &nd, uint32_t n0, uint32_t buf, Group4 &g) {
-  const size_t o = (size_t)buf * nd.N_pad;
-  g.Il = ld_na_i4(reinterpret_cast<const int4 *>(nd.acc_loc + o) + (n0 >> 2));
-  g.Ir = ld_na_i4(reinterpret_cast<const int4 *>(nd.acc_rem + o) + (n0 >> 2));
+  g.I = ld_na_i4(reinterpret_cast<const int4 *>(nd.acc + (size_t)buf * nd.N_pad) + (n0 >> 2));
 }
 
 // Advance the 4 neurons of g by step t (input buffers `buf`, read by
@@ -289,8 +285,7 @@ __device__ __forceinline__ uint32_t step4(const NetDev &nd, uint32_t n0, uint32_
     kx[q] = poisson_count(nd, pops[q], Wv[q]);
     local = (local + 1u == (uint32_t)kK) ? 0u : local + 1u;
   }
-  // int32 sums: the order of the terms does not change the result
-  int32_t Iv[4] = {g.Il.x + g.Ir.x, g.Il.y + g.Ir.y, g.Il.z + g.Ir.z, g.Il.w + g.Ir.w};
+  int32_t Iv[4] = {g.I.x, g.I.y, g.I.z, g.I.w};
 #pragma unroll
   for (int q = 0; q < 4; ++q)   // first external event: independent table loads
     if (kx[q]) Iv[q] += __ldg(nd.amp + pops[q] * kZTab + (Wv[q] & 0xFFFu));
@@ -311,7 +306,7 @@ __device__ __forceinline__ uint32_t step4(const NetDev &nd, uint32_t n0, uint32_
     reinterpret_cast<float4 *>(nd.V)[i4] = make_float4(Vv[0], Vv[1], Vv[2], Vv[3]);
     reinterpret_cast<float4 *>(nd.c)[i4] = make_float4(cv[0], cv[1], cv[2], cv[3]);
     reinterpret_cast<uint32_t *>(nd.ref)[i4] = rv[0] | (rv[1] << 8) | (rv[2] << 16) | (rv[3] << 24);
-    reinterpret_cast<int4 *>(nd.acc_rem + (size_t)buf * nd.N_pad)[i4] = make_int4(0, 0, 0, 0);
+    reinterpret_cast<int4 *>(nd.acc + (size_t)buf * nd.N_pad)[i4] = make_int4(0, 0, 0, 0);
   }
   return mask;
 }
@@ -326,32 +321,28 @@ __device__ __forceinline__ uint32_t update4(const NetDev &nd, uint32_t n0, uint3
 
 // Warp-level recording of the warp's spikes over G groups (all 32 lanes
 // active; in group g lane L owns neurons n0[g]..n0[g]+3, and the warp's 32
-// lanes cover one aligned 128-neuron tile).  Appends raster entries with one
-// returning atomic per warp, adds each spike to the step's history of its
-// module (one returning atomic per module the tile touches: a 128-neuron tile
-// lies in at most two 1250-neuron modules), counts rates with fire-and-forget
-// reductions, adds each tile's external events to that tile's slot and
-// prefetches into L2 the delay-group table and the first records of every
-// spiking neuron's row.  When `smem_list` is given the ids are also appended
-// there (block-local list for the fused step).
+// lanes cover one aligned 128-neuron tile).  Appends raster entries and the
+// step's spike list (`hist`) with one returning atomic each per warp, counts
+// rates with fire-and-forget reductions, adds each tile's external events to
+// that tile's slot and prefetches into L2 the delay-group table and the first
+// records of every spiking neuron's row.  When `smem_list` is given the ids
+// are also appended there (block-local list for the fused step).
 template <int G>
 __device__ __forceinline__ void record_warp(const NetDev &nd, const uint32_t (&mask)[G], const uint32_t (&n0)[G],
                                             const uint32_t (&n_ext)[G], uint32_t t, uint32_t k, uint32_t bin0,
                                             uint32_t *smem_list, uint32_t *smem_count) {
   const uint32_t lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
-  uint32_t below[G], gcnt[G], wtot = 0;
+  uint32_t before[G], wtot = 0;
 #pragma unroll
   for (int g = 0; g < G; ++g) {
-    below[g] = 0;
-    gcnt[g] = 0;
+    before[g] = wtot;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const uint32_t b = __ballot_sync(0xFFFFFFFFu, (mask[g] >> q) & 1u);
-      below[g] += __popc(b & lt);
-      gcnt[g] += __popc(b);
+      before[g] += __popc(b & lt);
+      wtot += __popc(b);
     }
-    wtot += gcnt[g];
     uint32_t ext = n_ext[g];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ext += __shfl_xor_sync(0xFFFFFFFFu, ext, o);
@@ -360,47 +351,24 @@ __device__ __forceinline__ void record_warp(const NetDev &nd, const uint32_t (&m
   }
   if (wtot == 0) return;
   const uint32_t slot = t % nd.D;
-  // spikes of each group in the tile's first module (ids below the boundary
-  // come first in the lane-major, neuron-minor order used for ranks)
-  uint32_t ma[G], nlo[G];
-#pragma unroll
-  for (int g = 0; g < G; ++g) {
-    ma[g] = __shfl_sync(0xFFFFFFFFu, n0[g], 0) / (uint32_t)kK;
-    const uint32_t bnd = (ma[g] + 1u) * (uint32_t)kK;
-    uint32_t mine = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) mine += ((mask[g] >> q) & 1u) && (n0[g] + q < bnd) ? 1u : 0u;
-    nlo[g] = __reduce_add_sync(0xFFFFFFFFu, mine);
-  }
-  uint32_t gbase = 0, sbase = 0, hlo[G], hhi[G];
-#pragma unroll
-  for (int g = 0; g < G; ++g) hlo[g] = hhi[g] = 0;
+  uint32_t gbase = 0, hbase = 0, sbase = 0;
   if (lane == 0) {
     gbase = atomicAdd(&nd.rec->cursor, wtot);
+    hbase = atomicAdd(nd.cnt + slot, wtot);
     if (smem_list) sbase = atomicAdd(smem_count, wtot);
-    uint32_t *hc = nd.hcnt + (size_t)slot * nd.G;
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      if (nlo[g]) hlo[g] = atomicAdd(hc + ma[g], nlo[g]);
-      if (gcnt[g] > nlo[g]) hhi[g] = atomicAdd(hc + ma[g] + 1u, gcnt[g] - nlo[g]);
-    }
   }
   gbase = __shfl_sync(0xFFFFFFFFu, gbase, 0);
+  hbase = __shfl_sync(0xFFFFFFFFu, hbase, 0);
   sbase = __shfl_sync(0xFFFFFFFFu, sbase, 0);
-#pragma unroll
-  for (int g = 0; g < G; ++g) {
-    hlo[g] = __shfl_sync(0xFFFFFFFFu, hlo[g], 0);
-    hhi[g] = __shfl_sync(0xFFFFFFFFu, hhi[g], 0);
-  }
   if (lane == 0 && gbase + wtot > nd.rec_cap) atomicOr(&nd.rec->status, kStatusRasterOverflow);
   const unsigned long long tag = ((unsigned long long)nd.slot << 48) | ((unsigned long long)k << 32);
   const uint32_t bin = t / nd.bin_steps - bin0;
   const uint32_t wb = nd.fmt ? 2u : 4u;
-  const uint32_t pre_keys = min(512u, nd.M_pad * 4u), pre_w = min(512u, nd.M_pad * wb);
-  uint32_t goff = 0;
+  const uint32_t pre_keys = min(256u, nd.M_pad * 4u), pre_w = min(256u, nd.M_pad * wb);
+  uint32_t *hist = nd.hist + (size_t)slot * nd.N_pad;
 #pragma unroll
   for (int g = 0; g < G; ++g) {
-    uint32_t r = below[g];   // rank of the lane's next spike within group g
+    uint32_t pos = before[g];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if ((mask[g] >> q) & 1u) {
@@ -410,71 +378,62 @@ __device__ __forceinline__ void record_warp(const NetDev &nd, const uint32_t (&m
         bulk_prefetch_l2(nd.offs + (size_t)id * nd.os, nd.os * 2u);
         bulk_prefetch_l2(row, pre_keys);
         bulk_prefetch_l2(row + (size_t)nd.M_pad * 4u, pre_w);
-        const uint32_t pos = goff + r;
         if (gbase + pos < nd.rec_cap) nd.rec_entries[gbase + pos] = tag | id;
+        hist[hbase + pos] = id;
         if (smem_list) smem_list[sbase + pos] = id;
         const uint32_t m = id / (uint32_t)kK;
-        const uint32_t hpos = (m == ma[g]) ? hlo[g] + r : hhi[g] + (r - nlo[g]);
-        nd.hist[(size_t)slot * nd.N + (size_t)m * kK + hpos] = id;
         red_add_u32(nd.rates + ((size_t)bin * nd.G + m) * 3u + pop_of_local(id - m * (uint32_t)kK), 1u);
-        ++r;
+        ++pos;
       }
     }
-    goff += gcnt[g];
   }
 }
 
 // ---------------------------------------------------------------------------
-// Delay-major delivery of one module (Sec. 2.1.1).  A delivery pass follows
-// the update of every step t with (t + 1) % kmin == 0 (kmin = the smallest
-// delay: the spikes of kmin consecutive steps are delivered together, the
-// paper's exchange step equal to the minimum delay).  It produces the inputs
-// of the next kmin steps T = t + 1 .. t + kmin: for each T and each delay d in
-// kmin..n_delay, the delay-d records of the module's spikes of step T - d.
+// Delay-major delivery (Sec. 2.1.1).  A delivery pass follows the update of
+// every step t with (t + 1) % kmin == 0 (kmin = the smallest delay: the spikes
+// of kmin consecutive steps are delivered together, the paper's exchange step
+// equal to the minimum delay).  It produces the inputs of the next kmin steps
+// T = t + 1 .. t + kmin: for each T, the delay-d group (kmin <= d <= n_delay)
+// of every spike of step T - d, one segment per (spike, d).  Segments are
+// spread over all warps of the grid, `lanes` lanes per segment, and their
+// records are reduced straight into the input buffer of T.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kSegCap = 512;   // (spike, delay) segments described per pass
-
-struct alignas(16) DeliverShared {
-  int32_t acc[kK + 2];        // input of the module's neurons from its own sources
-  uint32_t pre[260];          // pre[d]: segments with delay <= d (pre[0] = 0)
-  uint32_t src[kSegCap];      // source neuron of each segment of the pass
-  uint32_t rng[kSegCap];      // its records [lo, hi): lo | hi << 16
-};
+constexpr uint32_t kPreLen = 264;   // per-warp segment prefix over delays (n_delay <= 254)
 
 // Slot of step T - d, Tm = T mod D, 1 <= d < D.
 __device__ __forceinline__ uint32_t slot_back(uint32_t Tm, uint32_t d, uint32_t D) { return (Tm + D - d) % D; }
 
-// Add the records [a, b) of source s's row: targets inside the module
-// [mbase, mbase + 1250) into shared memory, the others into `rem`.
-__device__ __forceinline__ void add_records(const NetDev &nd, DeliverShared &sh, int32_t *rem, uint32_t s,
-                                            uint32_t a, uint32_t b, uint32_t sub, uint32_t lanes, uint32_t mbase) {
-  const uint8_t *row = nd.rows + (size_t)s * nd.row_bytes;
-  const uint32_t *keys = reinterpret_cast<const uint32_t *>(row);
-  const uint8_t *wrow = row + (size_t)nd.M_pad * 4u;
-  for (uint32_t r = a + sub; r < b; r += 4u * lanes) {
-    uint32_t kk[4];
-    int32_t vv[4];
+// One warp: pre[d] = spikes of steps T - d' summed over kmin <= d' <= d
+// (pre[d] = 0 below kmin), T = t + 1 + j with Tm = T mod D; the spikes of step
+// t itself are left out when skip_current.  Returns the total.
+__device__ __forceinline__ uint32_t warp_prefix(const NetDev &nd, uint32_t *pre, uint32_t Tm, uint32_t j,
+                                                bool skip_current) {
+  const uint32_t lane = lane_id();
+  const uint32_t D = nd.D, dmax = nd.n_delay, kmin = nd.kmin;
+  uint32_t v[8], sum = 0;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {   // the loads first, then the additions
-      const uint32_t rr = r + (uint32_t)u * lanes;
-      kk[u] = 0xFFFFFFFFu;
-      vv[u] = 0;
-      if (rr < b) {
-        kk[u] = ld_rec_u32(keys + rr);
-        vv[u] = nd.fmt ? ld_rec_s16(reinterpret_cast<const int16_t *>(wrow) + rr) * 64
-                       : __float2int_rn(__fmul_rn(ld_rec_f32(reinterpret_cast<const float *>(wrow) + rr), 65536.0f));
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (r + (uint32_t)u * lanes < b) {
-        const uint32_t tgt = kk[u] & 0xFFFFFFu;
-        const uint32_t lt = tgt - mbase;
-        if (lt < (uint32_t)kK) atomicAdd(&sh.acc[lt], vv[u]);
-        else red_add_s32(rem + tgt, vv[u]);
-      }
-    }
+  for (int i = 0; i < 8; ++i) {
+    const uint32_t d = lane * 8u + 1u + (uint32_t)i;
+    const bool use = d >= kmin && d <= dmax && !(skip_current && d == j + 1u);
+    v[i] = use ? nd.cnt[slot_back(Tm, d, D)] : 0u;
+    sum += v[i];
   }
+  uint32_t incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= (uint32_t)o) incl += y;
+  }
+  uint32_t acc = incl - sum;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    acc += v[i];
+    pre[lane * 8u + 1u + (uint32_t)i] = acc;
+  }
+  if (lane == 0) pre[0] = 0u;
+  __syncwarp();
+  return __shfl_sync(0xFFFFFFFFu, incl, 31);
 }
 
 // Prefetch into L2 the next delay group (after record b) of source s's row.
@@ -489,110 +448,75 @@ __device__ __forceinline__ void prefetch_next_group(const NetDev &nd, uint32_t s
   prefetch_range_l2(row + (size_t)nd.M_pad * 4u + (size_t)b * wb, (c2 - b) * wb);
 }
 
-// The delivery pass after step t for module m.  With skip_current the spikes
-// of step t are left out (the fused step delivers them from the blocks that
-// produced them, whose lists are complete before the module's history is).
-// Block-wide (every thread calls it with the same arguments); sh.acc is zero
-// on entry and on return.
-__device__ __forceinline__ void deliver_module(const NetDev &nd, DeliverShared &sh, uint32_t t, uint32_t m,
-                                               bool skip_current, uint32_t lanes) {
-  const uint32_t tid = threadIdx.x, nthr = blockDim.x;
-  const uint32_t D = nd.D, dmax = nd.n_delay, kmin = nd.kmin;
-  const uint32_t mbase = m * (uint32_t)kK;
-  const uint32_t grp = tid / lanes, sub = tid % lanes, ngrp = nthr / lanes;
-  for (uint32_t j = 0; j < kmin; ++j) {
-    const uint32_t T = t + 1u + j, Tm = T % D;   // target step
-    const uint32_t buf = T % nd.nbuf;
-    // 1. segments per delay and their prefix sums (one warp; n_delay <= 254)
-    if (tid < 32u) {
-      uint32_t v[8], sum = 0;
+// Reduce the records [a, b) of source s's row into `acc_T`, `lanes` lanes
+// (this lane is `sub`), the loads of four records per lane issued first.
+__device__ __forceinline__ void add_records(const NetDev &nd, int32_t *acc_T, uint32_t s, uint32_t a, uint32_t b,
+                                            uint32_t sub, uint32_t lanes) {
+  const uint8_t *row = nd.rows + (size_t)s * nd.row_bytes;
+  const uint32_t *keys = reinterpret_cast<const uint32_t *>(row);
+  const uint8_t *wrow = row + (size_t)nd.M_pad * 4u;
+  for (uint32_t r = a + sub; r < b; r += 4u * lanes) {
+    uint32_t kk[4];
+    int32_t vv[4];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const uint32_t d = tid * 8u + 1u + (uint32_t)i;
-        const bool use = d >= kmin && d <= dmax && !(skip_current && d == j + 1u);
-        v[i] = use ? nd.hcnt[(size_t)slot_back(Tm, d, D) * nd.G + m] : 0u;
-        sum += v[i];
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t rr = r + (uint32_t)u * lanes;
+      kk[u] = 0u;
+      vv[u] = 0;
+      if (rr < b) {
+        kk[u] = ld_rec_u32(keys + rr);
+        vv[u] = nd.fmt ? ld_rec_s16(reinterpret_cast<const int16_t *>(wrow) + rr) * 64
+                       : __float2int_rn(__fmul_rn(ld_rec_f32(reinterpret_cast<const float *>(wrow) + rr), 65536.0f));
       }
-      uint32_t incl = sum;
+    }
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (tid >= (uint32_t)o) incl += y;
-      }
-      uint32_t acc = incl - sum;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        acc += v[i];
-        sh.pre[tid * 8u + 1u + (uint32_t)i] = acc;
-      }
-      if (tid == 0) sh.pre[0] = 0u;
-    }
-    __syncthreads();
-    const uint32_t S = sh.pre[dmax];
-    int32_t *rem = nd.acc_rem + (size_t)buf * nd.N_pad;
-    for (uint32_t p0 = 0; p0 < S; p0 += kSegCap) {
-      const uint32_t np = min(kSegCap, S - p0);
-      // 2. describe the pass's segments: source, and its delay-d records
-      for (uint32_t q = tid; q < np; q += nthr) {
-        const uint32_t kseg = p0 + q;
-        uint32_t lo = 1u, hi = dmax;   // smallest d with pre[d] > kseg
-        while (lo < hi) {
-          const uint32_t mid = (lo + hi) >> 1;
-          if (sh.pre[mid] > kseg) hi = mid; else lo = mid + 1u;
-        }
-        const uint32_t d = lo, i = kseg - sh.pre[d - 1u];
-        const uint32_t s = nd.hist[(size_t)slot_back(Tm, d, D) * nd.N + mbase + i];
-        const uint16_t *o = nd.offs + (size_t)s * nd.os;
-        const uint32_t a = o[d - 1u], b = o[d];
-        sh.src[q] = s;
-        sh.rng[q] = a | (b << 16);
-        prefetch_next_group(nd, s, o, d, b);   // read at a later step
-      }
-      __syncthreads();
-      // 3. their records, `lanes` lanes per segment
-      for (uint32_t q = grp; q < np; q += ngrp)
-        add_records(nd, sh, rem, sh.src[q], sh.rng[q] & 0xFFFFu, sh.rng[q] >> 16, sub, lanes, mbase);
-      __syncthreads();
-    }
-    // 4. the module's own input of step T: one plain store per neuron
-    int2 *dst = reinterpret_cast<int2 *>(nd.acc_loc + (size_t)buf * nd.N_pad + mbase);
-    int2 *src = reinterpret_cast<int2 *>(sh.acc);
-    for (uint32_t i = tid; i < (uint32_t)kK / 2u; i += nthr) {
-      dst[i] = src[i];
-      src[i] = make_int2(0, 0);
-    }
-    __syncthreads();
+    for (int u = 0; u < 4; ++u)
+      if (r + (uint32_t)u * lanes < b) red_add_s32(acc_T + (kk[u] & 0xFFFFFFu), vv[u]);
   }
-  // the slots the next kmin steps append to (none of them read above)
-  for (uint32_t i = tid; i < kmin; i += nthr) nd.hcnt[(size_t)((t + 1u + i) % D) * nd.G + m] = 0u;
-  __syncthreads();
+}
+
+// Segments g = first, first + stride, ... < S of the target step with slot Tm
+// (prefix `pre` from warp_prefix), each by the `lanes` lanes of one group.
+__device__ __forceinline__ void deliver_segments(const NetDev &nd, const uint32_t *pre, uint32_t Tm, int32_t *acc_T,
+                                                 uint32_t S, uint32_t first, uint32_t stride, uint32_t sub,
+                                                 uint32_t lanes) {
+  const uint32_t D = nd.D, dmax = nd.n_delay;
+  for (uint32_t g = first; g < S; g += stride) {
+    uint32_t lo = 1u, hi = dmax;   // the segment's delay: smallest d with pre[d] > g
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (pre[mid] > g) hi = mid; else lo = mid + 1u;
+    }
+    const uint32_t d = lo, i = g - pre[d - 1u];
+    const uint32_t s = nd.hist[(size_t)slot_back(Tm, d, D) * nd.N_pad + i];
+    const uint16_t *o = nd.offs + (size_t)s * nd.os;
+    const uint32_t a = o[d - 1u], b = o[d];
+    if (sub == 0) prefetch_next_group(nd, s, o, d, b);   // read at a later pass
+    add_records(nd, acc_T, s, a, b, sub, lanes);
+  }
 }
 
 // Fused step, delivery pass after step t: the delay-kmin records of the
-// block's own spikes of step t, reduced straight into the remote buffer of
-// step t + kmin (the module's history of step t is not complete while other
-// blocks still update its neurons).
+// block's own spikes of step t, reduced into the input of step t + kmin (the
+// step's spike list is not complete while other blocks still update).
 __device__ void deliver_own(const NetDev &nd, const uint32_t *ids, uint32_t cnt, uint32_t t, uint32_t lanes) {
   const uint32_t tid = threadIdx.x;
   const uint32_t grp = tid / lanes, sub = tid % lanes, ngrp = blockDim.x / lanes;
   const uint32_t kmin = nd.kmin;
-  int32_t *rem = nd.acc_rem + (size_t)((t + kmin) % nd.nbuf) * nd.N_pad;
+  int32_t *acc_T = nd.acc + (size_t)((t + kmin) % nd.nbuf) * nd.N_pad;
   for (uint32_t j = grp; j < cnt; j += ngrp) {
     const uint32_t s = ids[j];
     const uint16_t *o = nd.offs + (size_t)s * nd.os;
     const uint32_t a = o[kmin - 1u], b = o[kmin];
-    const uint8_t *row = nd.rows + (size_t)s * nd.row_bytes;
-    const uint32_t *keys = reinterpret_cast<const uint32_t *>(row);
-    const uint8_t *wrow = row + (size_t)nd.M_pad * 4u;
     if (sub == 0) prefetch_next_group(nd, s, o, kmin, b);
-    for (uint32_t r = a + sub; r < b; r += lanes) {
-      const uint32_t key = ld_rec_u32(keys + r);
-      const int32_t v = nd.fmt ? ld_rec_s16(reinterpret_cast<const int16_t *>(wrow) + r) * 64
-                               : __float2int_rn(__fmul_rn(ld_rec_f32(reinterpret_cast<const float *>(wrow) + r),
-                                                          65536.0f));
-      red_add_s32(rem + (key & 0xFFFFFFu), v);
-    }
+    add_records(nd, acc_T, s, a, b, sub, lanes);
   }
+}
+
+// The counts of the slots the next kmin steps append to (none of them read by
+// the pass after step t).
+__device__ __forceinline__ void clear_next_counts(const NetDev &nd, uint32_t t) {
+  for (uint32_t i = threadIdx.x; i < nd.kmin; i += blockDim.x) nd.cnt[(t + 1u + i) % nd.D] = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -865,25 +789,34 @@ __global__ void __launch_bounds__(BLOCK, G == 1 ? 1280 / BLOCK : 1) k_update(con
 
 // ---------------------------------------------------------------------------
 // Kernel: delivery pass after step t (two-kernel path; the update kernel of
-// step t has completed the module histories).  Blocks take modules
-// m = blockIdx.x, blockIdx.x + gridDim.x, ...
+// step t has completed the step's spike list).  Every warp takes segments of
+// every target step of the pass.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256, 4) k_deliver(const __grid_constant__ NetDev nd, uint32_t k, uint32_t lanes) {
-  __shared__ DeliverShared sh;
+__global__ void __launch_bounds__(256) k_deliver(const __grid_constant__ NetDev nd, uint32_t k, uint32_t lanes) {
+  __shared__ uint32_t s_pre[8][kPreLen];
   const NetWin w = *nd.win;
   const uint32_t t = w.t0 + k;
   if (t >= w.t_end || (t + 1u) % nd.kmin != 0u) return;   // launched after the last step of an exchange period
-  for (uint32_t i = threadIdx.x; i < (uint32_t)kK + 2u; i += blockDim.x) sh.acc[i] = 0;
-  __syncthreads();
-  for (uint32_t m = blockIdx.x; m < nd.G; m += gridDim.x) deliver_module(nd, sh, t, m, false, lanes);
+  const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+  const uint32_t gpw = 32u / lanes, grp = lane / lanes, sub = lane % lanes;
+  const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+  const uint32_t gw = blockIdx.x * (blockDim.x >> 5) + warp;
+  uint32_t *pre = s_pre[warp];
+  for (uint32_t j = 0; j < nd.kmin; ++j) {
+    const uint32_t T = t + 1u + j;
+    const uint32_t S = warp_prefix(nd, pre, T % nd.D, j, false);
+    deliver_segments(nd, pre, T % nd.D, nd.acc + (size_t)(T % nd.nbuf) * nd.N_pad, S, gw * gpw + grp,
+                     nwarps * gpw, sub, lanes);
+    __syncwarp();   // every lane is done with pre before the next prefix
+  }
+  if (blockIdx.x == 0) clear_next_counts(nd, t);
 }
 
 // ---------------------------------------------------------------------------
 // Kernel: fused step over a table of networks.  A block takes work items
-// (network, 4*blockDim neurons, range of modules): update and recording with a
-// block-local spike list and, after the last step of an exchange period, the
-// delay-kmin records of those spikes and the rest of the item's modules'
-// input for the next kmin steps.  Update reads input buffer t % nbuf and
+// (network, 4*blockDim neurons): update and recording with a block-local spike
+// list and, after the last step of an exchange period, the delay-kmin records
+// of those spikes and the item's share of the rest of the network's pass.  Update reads input buffer t % nbuf and
 // delivery writes the buffers of steps t + 1 .. t + kmin (nbuf = kmin + 1:
 // never the one being read), so blocks need no grid-wide barrier; many small
 // blocks per SM let one block's update overlap another's delivery.  Launched with programmatic dependent launch: the
@@ -893,12 +826,11 @@ __global__ void __launch_bounds__(512) k_fused(const __grid_constant__ FusedTabl
   extern __shared__ __align__(128) uint8_t smem[];   // the item's spike ids (4 * blockDim)
   __shared__ NetDev nd;
   __shared__ NetWin s_win;
-  __shared__ DeliverShared sh;
+  __shared__ uint32_t s_pre[16][kPreLen];
   __shared__ uint32_t s_count;
   __shared__ uint32_t s_net;
   uint32_t *s_ids = reinterpret_cast<uint32_t *>(smem);
-  const uint32_t warp = threadIdx.x >> 5;
-  for (uint32_t i = threadIdx.x; i < (uint32_t)kK + 2u; i += blockDim.x) sh.acc[i] = 0;
+  const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
   if (threadIdx.x == 0) s_net = 0xFFFFFFFFu;
   bool waited = false;
   const uint32_t n_items = *tab.n_items;
@@ -931,8 +863,21 @@ __global__ void __launch_bounds__(512) k_fused(const __grid_constant__ FusedTabl
     }
     __syncthreads();
     if ((t + 1u) % nd.kmin == 0u) {   // the last step of an exchange period: delivery pass
-      deliver_own(nd, s_ids, s_count, t, tab.lanes);
-      for (uint32_t m = item.m_begin; m < item.m_end; ++m) deliver_module(nd, sh, t, m, true, tab.lanes);
+      const uint32_t lanes = tab.lanes;
+      deliver_own(nd, s_ids, s_count, t, lanes);
+      // the item's share of the pass: its network's segments are dealt over
+      // all groups of all the network's items
+      const uint32_t gpb = blockDim.x / lanes, gpw = 32u / lanes;
+      const uint32_t first = item.index * gpb + warp * gpw + lane / lanes, stride = item.count * gpb;
+      uint32_t *pre = s_pre[warp];
+      for (uint32_t j = 0; j < nd.kmin; ++j) {
+        const uint32_t T = t + 1u + j;
+        const uint32_t S = warp_prefix(nd, pre, T % nd.D, j, true);
+        deliver_segments(nd, pre, T % nd.D, nd.acc + (size_t)(T % nd.nbuf) * nd.N_pad, S, first, stride,
+                         lane % lanes, lanes);
+        __syncwarp();
+      }
+      if (item.index == 0) clear_next_counts(nd, t);
     }
   }
   if (!waited) {
