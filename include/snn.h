@@ -103,7 +103,7 @@ typedef struct snn_stats {
 typedef struct snn_launch {
   int32_t path;            /* 0 = two kernels per step (update, deliver); 1 = fused step kernel */
   int32_t update_block;    /* threads per update block: 64 (update_groups 1 only), 128, 256 or 512 */
-  int32_t deliver_warps;   /* warps per delivery block: 1..8 (a block delivers one module at a time) */
+  int32_t deliver_warps;   /* warps per delivery block: 1..16 */
   int32_t fused_block;     /* threads per fused-step block: 128..512 */
   int32_t fused_items_per_sm; /* fused blocks per SM to launch (1..32, capped by occupancy) */
   int32_t window_steps;    /* steps per captured CUDA graph (1..4096) */
@@ -115,9 +115,8 @@ typedef struct snn_launch {
                               context's persisting set-aside is raised to the device
                               maximum while any such network lives, then restored);
                               0 = normal caching */
-  int32_t deliver_blocks;  /* delivery blocks per SM: 1..32 (the grid is min(modules,
-                              SMs x deliver_blocks); blocks take several modules each
-                              when the grid has more modules than that) */
+  int32_t deliver_blocks;  /* delivery blocks per SM: 1..32 (the grid is SMs x deliver_blocks;
+                              every warp takes (spike, delay) segments of the pass) */
 } snn_launch;
 
 typedef void *(*snn_alloc_fn)(size_t bytes, void *ctx);

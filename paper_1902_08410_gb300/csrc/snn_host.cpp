@@ -468,8 +468,7 @@ static int sm_count_cached() {
   return v;
 }
 
-// Delivery grid: one block per module, at most deliver_blocks per SM (blocks
-// then take several modules each).
+// Delivery grid: deliver_blocks blocks per SM (every warp takes segments).
 static int deliver_grid(const snn_net *h);
 
 static void default_launch(snn_net *h) {
@@ -495,7 +494,7 @@ extern "C" int snn_footprint(const snn_params *p, size_t *bytes_out) {
 
 static int deliver_grid(const snn_net *h) {
   const int sms = h->sm_count > 0 ? h->sm_count : 148;
-  return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->L.G, (int64_t)sms * h->cfg.deliver_blocks));
+  return std::max(1, sms * h->cfg.deliver_blocks);
 }
 
 static void free_net(snn_net *h) {
@@ -1501,7 +1500,7 @@ extern "C" int snn_set_launch(snn_handle h, const snn_launch *cfg) {
   if (c.update_block != 64 && c.update_block != 128 && c.update_block != 256 && c.update_block != 512)
     return fail(SNN_ERR_ARG, "update_block must be 64, 128, 256 or 512");
   if (c.update_block == 64 && c.update_groups != 1) return fail(SNN_ERR_ARG, "update_block 64 takes update_groups 1");
-  if (c.deliver_warps < 1 || c.deliver_warps > 8) return fail(SNN_ERR_ARG, "deliver_warps must be in 1..8");
+  if (c.deliver_warps < 1 || c.deliver_warps > 16) return fail(SNN_ERR_ARG, "deliver_warps must be in 1..16");
   if (c.fused_block < 128 || c.fused_block > 512 || c.fused_block % 32)
     return fail(SNN_ERR_ARG, "fused_block must be a multiple of 32 in 128..512");
   if (c.fused_items_per_sm < 1 || c.fused_items_per_sm > 32) return fail(SNN_ERR_ARG, "fused_items_per_sm in 1..32");
@@ -1618,15 +1617,11 @@ static int autotune_impl(snn_net *h, uint32_t trial_steps, int path_only) {
   status = trial(orig, 3, &orig_ms);
   if (status == SNN_OK) run_cands();
   if (status == SNN_OK && best.path == 0) {
-    // stage 2: delivery shapes with the best update shape (blocks per SM
-    // matter only when the grid has more modules than the delivery grid)
+    // stage 2: delivery shapes with the best update shape
     cands.clear();
-    const int sms = h->sm_count > 0 ? h->sm_count : 148;
-    const bool many_modules = (int64_t)L.G > (int64_t)sms * 4;
-    for (int dw : {2, 4, 8})
-      for (int ln : {4, 8, 16, 32})
-        for (int db : {4, 8, 16}) {
-          if (!many_modules && db != best.deliver_blocks) continue;
+    for (int dw : {4, 8, 16})
+      for (int ln : {8, 16, 32})
+        for (int db : {2, 3, 4, 6, 8}) {
           snn_launch c = best;
           c.deliver_warps = dw;
           c.deliver_lanes = ln;

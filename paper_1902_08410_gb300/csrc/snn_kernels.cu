@@ -402,13 +402,13 @@ __device__ __forceinline__ void record_warp(const NetDev &nd, const uint32_t (&m
 constexpr uint32_t kPreLen = 264;   // per-warp segment prefix over delays (n_delay <= 254)
 
 // Slot of step T - d, Tm = T mod D, 1 <= d < D.
-__device__ __forceinline__ uint32_t slot_back(uint32_t Tm, uint32_t d, uint32_t D) { return (Tm + D - d) % D; }
+__device__ __forceinline__ uint32_t slot_back(uint32_t Tm, uint32_t d, uint32_t D) { return Tm >= d ? Tm - d : Tm + D - d; }
 
 // One warp: pre[d] = spikes of steps T - d' summed over kmin <= d' <= d
 // (pre[d] = 0 below kmin), T = t + 1 + j with Tm = T mod D; the spikes of step
-// t itself are left out when skip_current.  Returns the total.
-__device__ __forceinline__ uint32_t warp_prefix(const NetDev &nd, uint32_t *pre, uint32_t Tm, uint32_t j,
-                                                bool skip_current) {
+// t itself are left out when skip_current.  pre[kPreLen - 1] = the total.
+__device__ __forceinline__ void warp_prefix(const NetDev &nd, uint32_t *pre, uint32_t Tm, uint32_t j,
+                                            bool skip_current) {
   const uint32_t lane = lane_id();
   const uint32_t D = nd.D, dmax = nd.n_delay, kmin = nd.kmin;
   uint32_t v[8], sum = 0;
@@ -432,8 +432,7 @@ __device__ __forceinline__ uint32_t warp_prefix(const NetDev &nd, uint32_t *pre,
     pre[lane * 8u + 1u + (uint32_t)i] = acc;
   }
   if (lane == 0) pre[0] = 0u;
-  __syncwarp();
-  return __shfl_sync(0xFFFFFFFFu, incl, 31);
+  if (lane == 31) pre[kPreLen - 1] = incl;
 }
 
 // Prefetch into L2 the next delay group (after record b) of source s's row.
@@ -503,7 +502,9 @@ __device__ void deliver_own(const NetDev &nd, const uint32_t *ids, uint32_t cnt,
   const uint32_t tid = threadIdx.x;
   const uint32_t grp = tid / lanes, sub = tid % lanes, ngrp = blockDim.x / lanes;
   const uint32_t kmin = nd.kmin;
-  int32_t *acc_T = nd.acc + (size_t)((t + kmin) % nd.nbuf) * nd.N_pad;
+  uint32_t b = t % nd.nbuf + kmin;
+  b = b >= nd.nbuf ? b - nd.nbuf : b;
+  int32_t *acc_T = nd.acc + (size_t)b * nd.N_pad;
   for (uint32_t j = grp; j < cnt; j += ngrp) {
     const uint32_t s = ids[j];
     const uint16_t *o = nd.offs + (size_t)s * nd.os;
@@ -517,6 +518,18 @@ __device__ void deliver_own(const NetDev &nd, const uint32_t *ids, uint32_t cnt,
 // the pass after step t).
 __device__ __forceinline__ void clear_next_counts(const NetDev &nd, uint32_t t) {
   for (uint32_t i = threadIdx.x; i < nd.kmin; i += blockDim.x) nd.cnt[(t + 1u + i) % nd.D] = 0u;
+}
+
+// Target step T = t + 1 + j of the pass after step t: its slot T mod D and its
+// input buffer T mod nbuf, from tm = t mod D and tb = t mod nbuf (j < kmin < D,
+// kmin < nbuf: one wrap at most).
+__device__ __forceinline__ void target_of(const NetDev &nd, uint32_t tm, uint32_t tb, uint32_t j, uint32_t &Tm,
+                                          int32_t *&acc_T) {
+  Tm = tm + 1u + j;
+  Tm = Tm >= nd.D ? Tm - nd.D : Tm;
+  uint32_t b = tb + 1u + j;
+  b = b >= nd.nbuf ? b - nd.nbuf : b;
+  acc_T = nd.acc + (size_t)b * nd.N_pad;
 }
 
 // ---------------------------------------------------------------------------
@@ -792,8 +805,8 @@ __global__ void __launch_bounds__(BLOCK, G == 1 ? 1280 / BLOCK : 1) k_update(con
 // step t has completed the step's spike list).  Every warp takes segments of
 // every target step of the pass.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_deliver(const __grid_constant__ NetDev nd, uint32_t k, uint32_t lanes) {
-  __shared__ uint32_t s_pre[8][kPreLen];
+__global__ void __launch_bounds__(512) k_deliver(const __grid_constant__ NetDev nd, uint32_t k, uint32_t lanes) {
+  __shared__ uint32_t s_pre[16][kPreLen];
   const NetWin w = *nd.win;
   const uint32_t t = w.t0 + k;
   if (t >= w.t_end || (t + 1u) % nd.kmin != 0u) return;   // launched after the last step of an exchange period
@@ -801,13 +814,16 @@ __global__ void __launch_bounds__(256) k_deliver(const __grid_constant__ NetDev 
   const uint32_t gpw = 32u / lanes, grp = lane / lanes, sub = lane % lanes;
   const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
   const uint32_t gw = blockIdx.x * (blockDim.x >> 5) + warp;
-  uint32_t *pre = s_pre[warp];
+  const uint32_t tm = t % nd.D, tb = t % nd.nbuf;
+  uint32_t *pre = s_pre[warp];   // each warp its own prefix: no block barrier
   for (uint32_t j = 0; j < nd.kmin; ++j) {
-    const uint32_t T = t + 1u + j;
-    const uint32_t S = warp_prefix(nd, pre, T % nd.D, j, false);
-    deliver_segments(nd, pre, T % nd.D, nd.acc + (size_t)(T % nd.nbuf) * nd.N_pad, S, gw * gpw + grp,
-                     nwarps * gpw, sub, lanes);
-    __syncwarp();   // every lane is done with pre before the next prefix
+    uint32_t Tm;
+    int32_t *acc_T;
+    target_of(nd, tm, tb, j, Tm, acc_T);
+    warp_prefix(nd, pre, Tm, j, false);
+    __syncwarp();
+    deliver_segments(nd, pre, Tm, acc_T, pre[kPreLen - 1], gw * gpw + grp, nwarps * gpw, sub, lanes);
+    __syncwarp();   // every lane is done with the prefix before the next one
   }
   if (blockIdx.x == 0) clear_next_counts(nd, t);
 }
@@ -869,12 +885,15 @@ __global__ void __launch_bounds__(512) k_fused(const __grid_constant__ FusedTabl
       // all groups of all the network's items
       const uint32_t gpb = blockDim.x / lanes, gpw = 32u / lanes;
       const uint32_t first = item.index * gpb + warp * gpw + lane / lanes, stride = item.count * gpb;
+      const uint32_t tm = t % nd.D, tb = t % nd.nbuf;
       uint32_t *pre = s_pre[warp];
       for (uint32_t j = 0; j < nd.kmin; ++j) {
-        const uint32_t T = t + 1u + j;
-        const uint32_t S = warp_prefix(nd, pre, T % nd.D, j, true);
-        deliver_segments(nd, pre, T % nd.D, nd.acc + (size_t)(T % nd.nbuf) * nd.N_pad, S, first, stride,
-                         lane % lanes, lanes);
+        uint32_t Tm;
+        int32_t *acc_T;
+        target_of(nd, tm, tb, j, Tm, acc_T);
+        warp_prefix(nd, pre, Tm, j, true);
+        __syncwarp();
+        deliver_segments(nd, pre, Tm, acc_T, pre[kPreLen - 1], first, stride, lane % lanes, lanes);
         __syncwarp();
       }
       if (item.index == 0) clear_next_counts(nd, t);
@@ -977,7 +996,7 @@ cudaError_t launch_update(const NetDev &nd, uint32_t k, int block, int groups, c
 
 cudaError_t launch_deliver(const NetDev &nd, uint32_t k, uint32_t lanes, int warps, int blocks, const L2Window &l2,
                            cudaStream_t s) {
-  if (warps < 1 || warps > 8 || blocks < 1 || !valid_lanes(lanes)) return cudaErrorInvalidValue;
+  if (warps < 1 || warps > 16 || blocks < 1 || !valid_lanes(lanes)) return cudaErrorInvalidValue;
   return launch_ex(k_deliver, dim3((unsigned)blocks), dim3(warps * 32), 0, l2, s, nd, k, lanes);
 }
 
