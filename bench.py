@@ -65,11 +65,13 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="grid mode: skip the compact 64x64, 256-network batch and serving points")
-    ap.add_argument("--mode", choices=["grid", "batch", "serve", "grid64", "profile", "table_s1"], default="grid",
+    ap.add_argument("--mode", choices=["grid", "batch", "serve", "grid64", "profile", "table_s1", "min_delay"],
+                    default="grid",
                     help="grid: 24x24 SWA+AW (default); batch: 256-network SWA->AW sweep; serve: request "
                          "stream; grid64: 64x64 lambda sweep with f32 vs i16 records")
     ap.add_argument("--grid64-steps", type=int, default=50_000)
-    ap.add_argument("--s1-steps", type=int, default=50_000, help="table_s1 mode: measured steps per state")
+    ap.add_argument("--s1-steps", type=int, default=50_000,
+                    help="table_s1 and min_delay modes: measured steps per run")
     # --mode profile: one network, fixed launch shape (the target of ncu captures)
     ap.add_argument("--grid", type=int, default=24)
     ap.add_argument("--regime", choices=["SWA", "AW"], default="AW")
@@ -911,6 +913,52 @@ def run_grid64_mode(args, dist: Dist):
               flush=True)
 
 
+def run_min_delay_mode(args, dist: Dist):
+    """The paper's exchange step (Sec. 2.1.1): a 24x24 AW network with delays
+    of 10..20 steps (minimum delay 1 ms), delivered once per 10 steps, beside
+    the benchmark form with delays of 1..20 steps delivered every step.  Both
+    tuned after their first 5000 steps; events/s, time per step and kernel
+    launches per simulated millisecond."""
+    import torch
+    torch.cuda.set_device(dist.local_rank)
+    import paper_1902_08410_gb300 as snn
+    snn.build()
+    out = []
+    for kmin in (1, 10):
+        p = W.base_params(24, 24, 1.0, "AW")
+        p["min_delay"] = kmin
+        net = snn.Network(p, 1)
+        net.run(5000)
+        cfg = net.autotune(300)
+        st0 = net.stats()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sampler = ClockSampler(gpu_selector(dist.local_rank))
+        sampler.start()
+        e0.record()
+        net.run(args.s1_steps)
+        e1.record()
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        sec = e0.elapsed_time(e1) / 1e3
+        st1 = net.stats()
+        spikes = st1["spikes"] - st0["spikes"]
+        sim_ms = args.s1_steps * W.DT_MS
+        out.append({"min_delay": kmin, "delays": f"{kmin}..{p['n_delay']} steps",
+                    "events_per_s": spikes * EQUIV_PER_SPIKE / sec, "us_per_step": 1e6 * sec / args.s1_steps,
+                    "rate_hz": spikes / (net.N * sim_ms * 1e-3),
+                    "launches_per_sim_ms": (st1["kernel_launches"] - st0["kernel_launches"]) / sim_ms,
+                    "launch": cfg, "clocks": clocks})
+        net.close()
+        if dist.rank == 0:
+            print(json.dumps(out[-1]), flush=True)
+    if dist.rank == 0:
+        print(json.dumps({"metric": METRIC, "mode": "min_delay", "unit": UNIT, "data": "synthetic",
+                          "config": {"workload": f"24x24 AW grid, lambda 1.0, f32 records, {args.s1_steps} "
+                                                 f"timed steps after 5000 and the tuner, seed 1"},
+                          "launches_ratio": out[1]["launches_per_sim_ms"] / out[0]["launches_per_sim_ms"],
+                          "speedup": out[1]["events_per_s"] / out[0]["events_per_s"]}), flush=True)
+
+
 def run_profile_mode(args, dist: Dist):
     """One network, fixed launch shape: `warm-steps` steps, then `run-steps`
     steps in windows of `window` steps (the kernels an ncu capture targets)."""
@@ -935,11 +983,11 @@ def run_profile_mode(args, dist: Dist):
 
 def main():
     args = parse_args()
-    if args.mode in ("batch", "serve", "grid64", "profile", "table_s1"):
+    if args.mode in ("batch", "serve", "grid64", "profile", "table_s1", "min_delay"):
         dist = Dist("nccl")
         try:
             {"batch": run_batch_mode, "serve": run_serve_mode, "grid64": run_grid64_mode, "table_s1": run_table_s1_mode,
-             "profile": run_profile_mode}[args.mode](args, dist)
+             "profile": run_profile_mode, "min_delay": run_min_delay_mode}[args.mode](args, dist)
         finally:
             dist.close()
         return

@@ -10,7 +10,11 @@ import bench
 def test_committed_traffic_follows_kernel_source():
     """Traffic is reported from the capture while its source hash is the current
     one (read + write bytes per launch), and never for another source."""
-    with open(os.path.join(bench.ROOT, "profiles", "traffic.json")) as f:
+    path = os.path.join(bench.ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        assert bench.committed_traffic("k_update") is None and bench.committed_traffic("k_deliver") is None
+        return
+    with open(path) as f:
         t = json.load(f)
     current = t["kernel_source_sha256_16"] == bench.kernel_source_hash()
     for k in ("k_update", "k_deliver"):
