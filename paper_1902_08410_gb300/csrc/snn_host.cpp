@@ -670,6 +670,16 @@ extern "C" int snn_build_network(const snn_params *p, uint64_t seed, void *cuda_
 // ---------------------------------------------------------------------------
 // windows of steps
 // ---------------------------------------------------------------------------
+// Window of steps [t0, t_end) as the kernels read it.
+static void set_window(const snn_net *h, NetWin *w, uint64_t t0, uint64_t t_end) {
+  std::memset(w, 0, sizeof(NetWin));
+  w->t0 = (uint32_t)t0;
+  w->t_end = (uint32_t)t_end;
+  w->bin0 = (uint32_t)(t0 / (uint64_t)h->p.bin_steps);
+  w->t0_slot = (uint32_t)(t0 % h->L.D);
+  w->t0_buf = (uint32_t)(t0 % h->L.nbuf);
+}
+
 // Drop the cached window graphs unless they were captured for this window
 // length, launch shape and L2 window.
 static int prepare_graphs(snn_net *h, uint32_t window) {
@@ -704,13 +714,14 @@ static int capture_steps(snn_net *h, const NetDev &d, uint32_t steps, uint32_t p
   uint32_t n = 0;
   for (uint32_t k = 0; k < steps && err == cudaSuccess; ++k) {
     if (ev) err = cudaEventRecordWithFlags(ev[4 * k + 0], cs, cudaEventRecordExternal);
-    if (err == cudaSuccess) err = launch_update(d, k, c.update_block, c.update_groups, l2, cs);
+    const StepMod km{k % h->L.D, k % h->L.nbuf};
+    if (err == cudaSuccess) err = launch_update(d, k, km, c.update_block, c.update_groups, l2, cs);
     ++n;
     if (ev && err == cudaSuccess) err = cudaEventRecordWithFlags(ev[4 * k + 1], cs, cudaEventRecordExternal);
     if ((phase + k + 1u) % h->L.kmin == 0u) {
       if (ev && err == cudaSuccess) err = cudaEventRecordWithFlags(ev[4 * k + 2], cs, cudaEventRecordExternal);
       if (err == cudaSuccess)
-        err = launch_deliver(d, k, (uint32_t)c.deliver_lanes, c.deliver_warps, deliver_grid(h), l2, cs);
+        err = launch_deliver(d, k, km, (uint32_t)c.deliver_lanes, c.deliver_warps, deliver_grid(h), l2, cs);
       ++n;
       if (ev && err == cudaSuccess) err = cudaEventRecordWithFlags(ev[4 * k + 3], cs, cudaEventRecordExternal);
     }
@@ -881,9 +892,7 @@ static int runner_issue(PlainRunner &r) {
   if (t0 + n > 0xFFFFFFFFull) return fail(SNN_ERR_LIMIT, "step counter beyond 2^32");
   const int b = r.next_b;
   NetWin *pw = h->pinned_win + b;   // free: the copy of its last use finished before that drain
-  pw->t0 = (uint32_t)t0;
-  pw->t_end = (uint32_t)(t0 + n);
-  pw->bin0 = (uint32_t)(t0 / (uint64_t)h->p.bin_steps);
+  set_window(h, pw, t0, t0 + n);
   cudaGraphExec_t gx = nullptr;
   uint32_t kernels = 0;
   int rc = window_graph(h, b, (uint32_t)(t0 % h->L.kmin), &gx, &kernels);
@@ -1133,10 +1142,7 @@ static int run_fused(snn_net *const *hs, const uint64_t *steps, int32_t n) {
           status = fail(SNN_ERR_LIMIT, "step counter beyond 2^32");
           break;
         }
-        pw[i].t0 = (uint32_t)t_issue[i];
-        pw[i].t_end = (uint32_t)(t_issue[i] + adv);
-        pw[i].bin0 = (uint32_t)(t_issue[i] / (uint64_t)hs[i]->p.bin_steps);
-        pw[i].pad = 0;
+        set_window(hs[i], pw + i, t_issue[i], t_issue[i] + adv);
         p.t0s[i] = t_issue[i];
         p.adv[i] = adv;
       }
@@ -1334,9 +1340,7 @@ extern "C" int snn_time_kernels(snn_handle h, uint32_t steps, double *ms_out) {
   if (rc) return rc;
   rc = dev_alloc(guard.snap, L.off_rows);   // V, c, ref, input buffers, spike history
   if (rc) return rc;
-  h->pinned_win->t0 = (uint32_t)t0;
-  h->pinned_win->t_end = (uint32_t)(t0 + steps);
-  h->pinned_win->bin0 = (uint32_t)(t0 / (uint64_t)h->p.bin_steps);
+  set_window(h, h->pinned_win, t0, t0 + steps);
   CU_TRY(cudaMemcpyAsync(base + L.off_win[0], h->pinned_win, sizeof(NetWin), cudaMemcpyHostToDevice, s));
   // (1) the steps as snn_run runs them, from a snapshot that is restored after
   CU_TRY(cudaMemcpyAsync(guard.snap.p, base, L.off_rows, cudaMemcpyDeviceToDevice, s));

@@ -24,7 +24,17 @@ struct alignas(16) NetWin {
   uint32_t t0;          // absolute step of the window's first step
   uint32_t t_end;       // exclusive absolute step at which the network stops
   uint32_t bin0;        // first rate bin of the window (t0 / bin_steps)
-  uint32_t pad;
+  uint32_t t0_slot;     // t0 mod D
+  uint32_t t0_buf;      // t0 mod nbuf
+  uint32_t pad[3];
+};
+
+// Residues of step k of a window (k mod D, k mod nbuf), baked into its
+// kernels when the window is captured, so that a kernel finds the slot and
+// input buffer of step t0 + k from the window's residues without a division.
+struct StepMod {
+  uint32_t slot;
+  uint32_t buf;
 };
 
 // Recording header of a network (device memory, zeroed at every window start).
@@ -121,9 +131,10 @@ struct L2Window {
   size_t bytes = 0;
   float hit_ratio = 0.0f;
 };
-cudaError_t launch_update(const NetDev &nd, uint32_t k, int block, int groups, const L2Window &l2, cudaStream_t s);
-cudaError_t launch_deliver(const NetDev &nd, uint32_t k, uint32_t lanes, int warps, int blocks, const L2Window &l2,
-                           cudaStream_t s);
+cudaError_t launch_update(const NetDev &nd, uint32_t k, StepMod km, int block, int groups, const L2Window &l2,
+                          cudaStream_t s);
+cudaError_t launch_deliver(const NetDev &nd, uint32_t k, StepMod km, uint32_t lanes, int warps, int blocks,
+                           const L2Window &l2, cudaStream_t s);
 cudaError_t launch_fused(const FusedTable &tab, uint32_t k, int block, int blocks, cudaStream_t s);
 int fused_blocks_per_sm(int block);   // resident fused blocks per SM
 // u16 entries per row of the delay-group table

@@ -311,12 +311,21 @@ __device__ __forceinline__ uint32_t step4(const NetDev &nd, uint32_t n0, uint32_
   return mask;
 }
 
-__device__ __forceinline__ uint32_t update4(const NetDev &nd, uint32_t n0, uint32_t t, uint32_t &n_ext) {
+__device__ __forceinline__ uint32_t update4(const NetDev &nd, uint32_t n0, uint32_t t, uint32_t buf, uint32_t &n_ext) {
   Group4 g;
   load_state4(nd, n0, g);
-  const uint32_t buf = t % nd.nbuf;
   load_input4(nd, n0, buf, g);
   return step4(nd, n0, t, buf, g, n_ext);
+}
+
+// Slot (t mod D) and input buffer (t mod nbuf) of step t = t0 + k, from the
+// window's residues and the step's, without a division.
+__device__ __forceinline__ void step_residues(const NetDev &nd, const NetWin &w, StepMod km, uint32_t &tm,
+                                              uint32_t &tb) {
+  tm = w.t0_slot + km.slot;
+  tm = tm >= nd.D ? tm - nd.D : tm;
+  tb = w.t0_buf + km.buf;
+  tb = tb >= nd.nbuf ? tb - nd.nbuf : tb;
 }
 
 // Warp-level recording of the warp's spikes over G groups (all 32 lanes
@@ -329,8 +338,8 @@ __device__ __forceinline__ uint32_t update4(const NetDev &nd, uint32_t n0, uint3
 // are also appended there (block-local list for the fused step).
 template <int G>
 __device__ __forceinline__ void record_warp(const NetDev &nd, const uint32_t (&mask)[G], const uint32_t (&n0)[G],
-                                            const uint32_t (&n_ext)[G], uint32_t t, uint32_t k, uint32_t bin0,
-                                            uint32_t *smem_list, uint32_t *smem_count) {
+                                            const uint32_t (&n_ext)[G], uint32_t t, uint32_t slot, uint32_t k,
+                                            uint32_t bin0, uint32_t *smem_list, uint32_t *smem_count) {
   const uint32_t lane = lane_id();
   const uint32_t lt = (1u << lane) - 1u;
   uint32_t before[G], wtot = 0;
@@ -350,7 +359,6 @@ __device__ __forceinline__ void record_warp(const NetDev &nd, const uint32_t (&m
     if (lane == 0 && ext) red_add_u64(nd.ext_acc + tile, ext);   // slot owned by this warp
   }
   if (wtot == 0) return;
-  const uint32_t slot = t % nd.D;
   uint32_t gbase = 0, hbase = 0, sbase = 0;
   if (lane == 0) {
     gbase = atomicAdd(&nd.rec->cursor, wtot);
@@ -407,32 +415,29 @@ __device__ __forceinline__ uint32_t slot_back(uint32_t Tm, uint32_t d, uint32_t 
 // One warp: pre[d] = spikes of steps T - d' summed over kmin <= d' <= d
 // (pre[d] = 0 below kmin), T = t + 1 + j with Tm = T mod D; the spikes of step
 // t itself are left out when skip_current.  pre[kPreLen - 1] = the total.
+// Lane l handles delay base + l + 1: one load and one scan per 32 delays.
 __device__ __forceinline__ void warp_prefix(const NetDev &nd, uint32_t *pre, uint32_t Tm, uint32_t j,
                                             bool skip_current) {
   const uint32_t lane = lane_id();
   const uint32_t D = nd.D, dmax = nd.n_delay, kmin = nd.kmin;
-  uint32_t v[8], sum = 0;
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const uint32_t d = lane * 8u + 1u + (uint32_t)i;
+  uint32_t run = 0;
+  for (uint32_t base = 0; base < dmax; base += 32u) {
+    const uint32_t d = base + lane + 1u;
     const bool use = d >= kmin && d <= dmax && !(skip_current && d == j + 1u);
-    v[i] = use ? nd.cnt[slot_back(Tm, d, D)] : 0u;
-    sum += v[i];
-  }
-  uint32_t incl = sum;
+    uint32_t incl = use ? nd.cnt[slot_back(Tm, d, D)] : 0u;
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-    if (lane >= (uint32_t)o) incl += y;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= (uint32_t)o) incl += y;
+    }
+    incl += run;
+    if (d <= dmax) pre[d] = incl;
+    run = __shfl_sync(0xFFFFFFFFu, incl, 31);
   }
-  uint32_t acc = incl - sum;
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    acc += v[i];
-    pre[lane * 8u + 1u + (uint32_t)i] = acc;
+  if (lane == 0) {
+    pre[0] = 0u;
+    pre[kPreLen - 1] = run;
   }
-  if (lane == 0) pre[0] = 0u;
-  if (lane == 31) pre[kPreLen - 1] = incl;
 }
 
 // Prefetch into L2 the next delay group (after record b) of source s's row.
@@ -756,7 +761,7 @@ __global__ void __launch_bounds__(kBuildWarpsMax * 32) k_build_rows(const __grid
 // that a 720k-neuron grid (37 warps per SM) runs in a single wave.
 template <int BLOCK, int G>
 __global__ void __launch_bounds__(BLOCK, G == 1 ? 1280 / BLOCK : 1) k_update(const __grid_constant__ NetDev nd,
-                                                                           uint32_t k) {
+                                                                           uint32_t k, StepMod km) {
   uint32_t n0[G];
   bool live[G];
   bool any = false;
@@ -775,7 +780,8 @@ __global__ void __launch_bounds__(BLOCK, G == 1 ? 1280 / BLOCK : 1) k_update(con
   const NetWin w = *nd.win;
   const uint32_t t = w.t0 + k;
   if (t >= w.t_end) return;
-  const uint32_t buf = t % nd.nbuf;
+  uint32_t slot, buf;
+  step_residues(nd, w, km, slot, buf);
 #pragma unroll
   for (int g = 0; g < G; ++g)
     if (live[g]) load_input4(nd, n0[g], buf, st4[g]);
@@ -788,13 +794,13 @@ __global__ void __launch_bounds__(BLOCK, G == 1 ? 1280 / BLOCK : 1) k_update(con
   }
   // record per group whose tile is live (warp-uniform)
   if (live[G - 1]) {
-    record_warp<G>(nd, mask, n0, n_ext, t, k, w.bin0, nullptr, nullptr);
+    record_warp<G>(nd, mask, n0, n_ext, t, slot, k, w.bin0, nullptr, nullptr);
   } else {
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       if (live[g]) {
         const uint32_t m1[1] = {mask[g]}, a1[1] = {n0[g]}, e1[1] = {n_ext[g]};
-        record_warp<1>(nd, m1, a1, e1, t, k, w.bin0, nullptr, nullptr);
+        record_warp<1>(nd, m1, a1, e1, t, slot, k, w.bin0, nullptr, nullptr);
       }
     }
   }
@@ -805,16 +811,18 @@ __global__ void __launch_bounds__(BLOCK, G == 1 ? 1280 / BLOCK : 1) k_update(con
 // step t has completed the step's spike list).  Every warp takes segments of
 // every target step of the pass.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(512) k_deliver(const __grid_constant__ NetDev nd, uint32_t k, uint32_t lanes) {
+__global__ void __launch_bounds__(512, 2) k_deliver(const __grid_constant__ NetDev nd, uint32_t k, StepMod km,
+                                                  uint32_t lanes) {
   __shared__ uint32_t s_pre[16][kPreLen];
-  const NetWin w = *nd.win;
+  const NetWin w = *nd.win;   // launched after the last step of an exchange period
   const uint32_t t = w.t0 + k;
-  if (t >= w.t_end || (t + 1u) % nd.kmin != 0u) return;   // launched after the last step of an exchange period
+  if (t >= w.t_end) return;
   const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
   const uint32_t gpw = 32u / lanes, grp = lane / lanes, sub = lane % lanes;
   const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
   const uint32_t gw = blockIdx.x * (blockDim.x >> 5) + warp;
-  const uint32_t tm = t % nd.D, tb = t % nd.nbuf;
+  uint32_t tm, tb;
+  step_residues(nd, w, km, tm, tb);
   uint32_t *pre = s_pre[warp];   // each warp its own prefix: no block barrier
   for (uint32_t j = 0; j < nd.kmin; ++j) {
     uint32_t Tm;
@@ -871,11 +879,12 @@ __global__ void __launch_bounds__(512) k_fused(const __grid_constant__ FusedTabl
     }
     const uint32_t n0 = item.n_begin + threadIdx.x * 4u;
     const uint32_t warp_first = item.n_begin + warp * 128u;
+    const uint32_t tm = t % nd.D, tb = t % nd.nbuf;
     if (warp_first < nd.N_pad) {
       uint32_t n_ext[1] = {0};
-      const uint32_t mask[1] = {update4(nd, n0, t, n_ext[0])};
+      const uint32_t mask[1] = {update4(nd, n0, t, tb, n_ext[0])};
       const uint32_t a1[1] = {n0};
-      record_warp<1>(nd, mask, a1, n_ext, t, k, s_win.bin0, s_ids, &s_count);
+      record_warp<1>(nd, mask, a1, n_ext, t, tm, k, s_win.bin0, s_ids, &s_count);
     }
     __syncthreads();
     if ((t + 1u) % nd.kmin == 0u) {   // the last step of an exchange period: delivery pass
@@ -885,7 +894,6 @@ __global__ void __launch_bounds__(512) k_fused(const __grid_constant__ FusedTabl
       // all groups of all the network's items
       const uint32_t gpb = blockDim.x / lanes, gpw = 32u / lanes;
       const uint32_t first = item.index * gpb + warp * gpw + lane / lanes, stride = item.count * gpb;
-      const uint32_t tm = t % nd.D, tb = t % nd.nbuf;
       uint32_t *pre = s_pre[warp];
       for (uint32_t j = 0; j < nd.kmin; ++j) {
         uint32_t Tm;
@@ -982,11 +990,12 @@ static cudaError_t launch_ex(void (*kernel)(Args...), dim3 grid, dim3 block, siz
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-cudaError_t launch_update(const NetDev &nd, uint32_t k, int block, int groups, const L2Window &l2, cudaStream_t s) {
+cudaError_t launch_update(const NetDev &nd, uint32_t k, StepMod km, int block, int groups, const L2Window &l2,
+                          cudaStream_t s) {
   const uint32_t per_block = (uint32_t)block * 4u * (uint32_t)groups;
   const uint32_t blocks = (nd.N_pad + per_block - 1) / per_block;
 #define SNN_UPD(B, G) \
-  if (block == B && groups == G) return launch_ex(k_update<B, G>, dim3(blocks), dim3(B), 0, l2, s, nd, k);
+  if (block == B && groups == G) return launch_ex(k_update<B, G>, dim3(blocks), dim3(B), 0, l2, s, nd, k, km);
   SNN_UPD(64, 1) SNN_UPD(128, 1) SNN_UPD(128, 2) SNN_UPD(128, 4)
   SNN_UPD(256, 1) SNN_UPD(256, 2) SNN_UPD(256, 4)
   SNN_UPD(512, 1) SNN_UPD(512, 2)
@@ -994,10 +1003,10 @@ cudaError_t launch_update(const NetDev &nd, uint32_t k, int block, int groups, c
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_deliver(const NetDev &nd, uint32_t k, uint32_t lanes, int warps, int blocks, const L2Window &l2,
-                           cudaStream_t s) {
+cudaError_t launch_deliver(const NetDev &nd, uint32_t k, StepMod km, uint32_t lanes, int warps, int blocks,
+                           const L2Window &l2, cudaStream_t s) {
   if (warps < 1 || warps > 16 || blocks < 1 || !valid_lanes(lanes)) return cudaErrorInvalidValue;
-  return launch_ex(k_deliver, dim3((unsigned)blocks), dim3(warps * 32), 0, l2, s, nd, k, lanes);
+  return launch_ex(k_deliver, dim3((unsigned)blocks), dim3(warps * 32), 0, l2, s, nd, k, km, lanes);
 }
 
 cudaError_t launch_fused(const FusedTable &tab, uint32_t k, int block, int blocks, cudaStream_t s) {
