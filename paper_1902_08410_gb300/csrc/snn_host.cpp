@@ -310,7 +310,7 @@ static Layout make_layout(const snn_params &p) {
   L.M = (uint32_t)p.out_degree;
   L.M_pad = (uint32_t)align_up(L.M, 8);
   L.kmin = (uint32_t)(p.min_delay < 1 ? 1 : p.min_delay);
-  L.nbuf = L.kmin + 1u;
+  L.nbuf = 2u * L.kmin;   // >= kmin + 1; windows of one graph start at the same t0 mod nbuf
   L.D = (uint32_t)p.n_delay + L.kmin;
   L.row_bytes = L.M_pad * 4u + L.M_pad * (p.record_format == SNN_REC_I16 ? 2u : 4u);
   L.os = offs_stride((uint32_t)p.n_delay);
@@ -372,7 +372,8 @@ struct snn_net {
   cudaEvent_t ev_block[2] = {nullptr, nullptr};   // recording block b copied to the host
   snn_launch cfg{};
   // window graphs of the two-kernel path, per buffer set and phase of the
-  // window's first step within an exchange period (t0 % kmin), captured lazily
+  // window's first step (t0 % nbuf, which fixes its input buffers and its
+  // position in the exchange period), captured lazily
   std::vector<cudaGraphExec_t> exec[2];
   std::vector<uint32_t> exec_kernels[2];   // kernels launched by each graph
   uint32_t exec_window = 0;
@@ -677,7 +678,6 @@ static void set_window(const snn_net *h, NetWin *w, uint64_t t0, uint64_t t_end)
   w->t_end = (uint32_t)t_end;
   w->bin0 = (uint32_t)(t0 / (uint64_t)h->p.bin_steps);
   w->t0_slot = (uint32_t)(t0 % h->L.D);
-  w->t0_buf = (uint32_t)(t0 % h->L.nbuf);
 }
 
 // Drop the cached window graphs unless they were captured for this window
@@ -687,13 +687,13 @@ static int prepare_graphs(snn_net *h, uint32_t window) {
   int rc = l2_window(h, &l2);
   if (rc) return rc;
   if (h->exec_window == window && h->exec_l2_ratio == l2.hit_ratio &&
-      std::memcmp(&h->exec_cfg, &h->cfg, sizeof(snn_launch)) == 0 && h->exec[0].size() == h->L.kmin)
+      std::memcmp(&h->exec_cfg, &h->cfg, sizeof(snn_launch)) == 0 && h->exec[0].size() == h->L.nbuf)
     return SNN_OK;
   for (int b = 0; b < 2; ++b) {
     for (auto e : h->exec[b])
       if (e) cudaGraphExecDestroy(e);
-    h->exec[b].assign(h->L.kmin, nullptr);
-    h->exec_kernels[b].assign(h->L.kmin, 0u);
+    h->exec[b].assign(h->L.nbuf, nullptr);
+    h->exec_kernels[b].assign(h->L.nbuf, 0u);
   }
   h->exec_window = window;
   h->exec_cfg = h->cfg;
@@ -702,7 +702,7 @@ static int prepare_graphs(snn_net *h, uint32_t window) {
 }
 
 // Capture the steps k = 0..steps-1 of a window starting at a step with
-// phase = t0 % kmin: the update of every step, the delivery pass after every
+// phase = t0 % nbuf: the update of every step, the delivery pass after every
 // step t with (t + 1) % kmin == 0.  With `ev`, event record nodes bracket every
 // kernel (ev[4k..4k+3]: update start/end, delivery start/end).
 static int capture_steps(snn_net *h, const NetDev &d, uint32_t steps, uint32_t phase, const L2Window &l2,
@@ -714,7 +714,7 @@ static int capture_steps(snn_net *h, const NetDev &d, uint32_t steps, uint32_t p
   uint32_t n = 0;
   for (uint32_t k = 0; k < steps && err == cudaSuccess; ++k) {
     if (ev) err = cudaEventRecordWithFlags(ev[4 * k + 0], cs, cudaEventRecordExternal);
-    const StepMod km{k % h->L.D, k % h->L.nbuf};
+    const StepMod km{k % h->L.D, (phase + k) % h->L.nbuf};
     if (err == cudaSuccess) err = launch_update(d, k, km, c.update_block, c.update_groups, l2, cs);
     ++n;
     if (ev && err == cudaSuccess) err = cudaEventRecordWithFlags(ev[4 * k + 1], cs, cudaEventRecordExternal);
@@ -895,7 +895,7 @@ static int runner_issue(PlainRunner &r) {
   set_window(h, pw, t0, t0 + n);
   cudaGraphExec_t gx = nullptr;
   uint32_t kernels = 0;
-  int rc = window_graph(h, b, (uint32_t)(t0 % h->L.kmin), &gx, &kernels);
+  int rc = window_graph(h, b, (uint32_t)(t0 % h->L.nbuf), &gx, &kernels);
   if (rc) return rc;
   CU_TRY(cudaMemcpyAsync(base + h->L.off_win[b], pw, sizeof(NetWin), cudaMemcpyHostToDevice, h->stream));
   CU_TRY(cudaGraphLaunch(gx, h->stream));
@@ -1332,7 +1332,7 @@ extern "C" int snn_time_kernels(snn_handle h, uint32_t steps, double *ms_out) {
     }
   } guard{&ev};
   guard.s = s;
-  const uint32_t phase = (uint32_t)(t0 % L.kmin);
+  const uint32_t phase = (uint32_t)(t0 % L.nbuf);
   uint32_t kernels = 0;
   rc = capture_steps(h, descriptor(h, 0), steps, phase, l2, nullptr, &guard.gx[0], &kernels);
   if (rc) return rc;

@@ -25,16 +25,17 @@ struct alignas(16) NetWin {
   uint32_t t_end;       // exclusive absolute step at which the network stops
   uint32_t bin0;        // first rate bin of the window (t0 / bin_steps)
   uint32_t t0_slot;     // t0 mod D
-  uint32_t t0_buf;      // t0 mod nbuf
-  uint32_t pad[3];
+  uint32_t pad[4];
 };
 
-// Residues of step k of a window (k mod D, k mod nbuf), baked into its
-// kernels when the window is captured, so that a kernel finds the slot and
-// input buffer of step t0 + k from the window's residues without a division.
+// Baked into the kernels of step k of a window when the window is captured
+// (windows of one graph all start at the same t0 mod nbuf): k mod D, from
+// which a kernel finds the slot of step t0 + k with the window's t0_slot and
+// no division, and the input buffer of step t0 + k itself, known before the
+// window is read.
 struct StepMod {
-  uint32_t slot;
-  uint32_t buf;
+  uint32_t slot;        // k mod D
+  uint32_t buf;         // (t0 + k) mod nbuf
 };
 
 // Recording header of a network (device memory, zeroed at every window start).
@@ -64,7 +65,7 @@ struct alignas(16) NetDev {
   uint32_t n_delay;     // largest delay in steps
   uint32_t os;          // u16 entries per row of the delay-group table (multiple of 8)
   uint32_t kmin;        // smallest delay: steps per exchange period (delivery after steps t with (t + 1) % kmin == 0)
-  uint32_t nbuf;        // input buffers = kmin + 1 (the input of step t is buffer t % nbuf)
+  uint32_t nbuf;        // input buffers = 2 kmin (the input of step t is buffer t % nbuf)
   uint32_t pad1;
 
   // --- per population constants (Eq. 2 propagators, Table S1)

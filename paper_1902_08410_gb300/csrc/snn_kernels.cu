@@ -182,6 +182,7 @@ __device__ __forceinline__ int32_t extra_sum(const NetDev &nd, int pop, uint32_t
 // Called by whole warps (all 32 lanes).
 __device__ __forceinline__ void extra_events_warp(const NetDev &nd, uint32_t n0, uint32_t t, const uint32_t (&kx)[4],
                                                   int32_t (&Iv)[4]) {
+  if (!__any_sync(0xFFFFFFFFu, kx[0] > 1u || kx[1] > 1u || kx[2] > 1u || kx[3] > 1u)) return;   // most warps
   const uint32_t lane = lane_id(), lt = (1u << lane) - 1u;
   uint32_t bal[4], idx[4], cnt[4], total = 0;
 #pragma unroll
@@ -318,14 +319,11 @@ __device__ __forceinline__ uint32_t update4(const NetDev &nd, uint32_t n0, uint3
   return step4(nd, n0, t, buf, g, n_ext);
 }
 
-// Slot (t mod D) and input buffer (t mod nbuf) of step t = t0 + k, from the
-// window's residues and the step's, without a division.
-__device__ __forceinline__ void step_residues(const NetDev &nd, const NetWin &w, StepMod km, uint32_t &tm,
-                                              uint32_t &tb) {
-  tm = w.t0_slot + km.slot;
-  tm = tm >= nd.D ? tm - nd.D : tm;
-  tb = w.t0_buf + km.buf;
-  tb = tb >= nd.nbuf ? tb - nd.nbuf : tb;
+// Slot (t mod D) of step t = t0 + k from the window's residue and the step's,
+// without a division.
+__device__ __forceinline__ uint32_t step_slot(const NetDev &nd, const NetWin &w, StepMod km) {
+  const uint32_t tm = w.t0_slot + km.slot;
+  return tm >= nd.D ? tm - nd.D : tm;
 }
 
 // Warp-level recording of the warp's spikes over G groups (all 32 lanes
@@ -527,7 +525,7 @@ __device__ __forceinline__ void clear_next_counts(const NetDev &nd, uint32_t t) 
 
 // Target step T = t + 1 + j of the pass after step t: its slot T mod D and its
 // input buffer T mod nbuf, from tm = t mod D and tb = t mod nbuf (j < kmin < D,
-// kmin < nbuf: one wrap at most).
+// kmin < nbuf = 2 kmin: one wrap at most).
 __device__ __forceinline__ void target_of(const NetDev &nd, uint32_t tm, uint32_t tb, uint32_t j, uint32_t &Tm,
                                           int32_t *&acc_T) {
   Tm = tm + 1u + j;
@@ -776,15 +774,14 @@ __global__ void __launch_bounds__(BLOCK, G == 1 ? 1280 / BLOCK : 1) k_update(con
   Group4 st4[G];
 #pragma unroll
   for (int g = 0; g < G; ++g)
-    if (live[g]) load_state4(nd, n0[g], st4[g]);
+    if (live[g]) {   // the state and the step's input buffer, before the window is read
+      load_state4(nd, n0[g], st4[g]);
+      load_input4(nd, n0[g], km.buf, st4[g]);
+    }
   const NetWin w = *nd.win;
   const uint32_t t = w.t0 + k;
   if (t >= w.t_end) return;
-  uint32_t slot, buf;
-  step_residues(nd, w, km, slot, buf);
-#pragma unroll
-  for (int g = 0; g < G; ++g)
-    if (live[g]) load_input4(nd, n0[g], buf, st4[g]);
+  const uint32_t slot = step_slot(nd, w, km), buf = km.buf;
   uint32_t mask[G], n_ext[G];
 #pragma unroll
   for (int g = 0; g < G; ++g) {
@@ -821,8 +818,7 @@ __global__ void __launch_bounds__(512, 2) k_deliver(const __grid_constant__ NetD
   const uint32_t gpw = 32u / lanes, grp = lane / lanes, sub = lane % lanes;
   const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
   const uint32_t gw = blockIdx.x * (blockDim.x >> 5) + warp;
-  uint32_t tm, tb;
-  step_residues(nd, w, km, tm, tb);
+  const uint32_t tm = step_slot(nd, w, km), tb = km.buf;
   uint32_t *pre = s_pre[warp];   // each warp its own prefix: no block barrier
   for (uint32_t j = 0; j < nd.kmin; ++j) {
     uint32_t Tm;
