@@ -117,6 +117,11 @@ typedef struct snn_launch {
                               0 = normal caching */
   int32_t deliver_blocks;  /* delivery blocks per SM: 1..32 (the grid is SMs x deliver_blocks;
                               every warp takes (spike, delay) segments of the pass) */
+  int32_t overlap;         /* two-kernel path: 1 = the kernels of consecutive steps overlap
+                              (programmatic dependent launch: a delivery pass starts on the
+                              spikes of earlier steps while the update still runs, and the
+                              next update computes its external drive while the pass
+                              finishes); 0 = every kernel starts after the previous one ends */
 } snn_launch;
 
 typedef void *(*snn_alloc_fn)(size_t bytes, void *ctx);

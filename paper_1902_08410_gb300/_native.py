@@ -96,7 +96,7 @@ class SnnLaunch(ctypes.Structure):
                 ("fused_block", ctypes.c_int32), ("fused_items_per_sm", ctypes.c_int32),
                 ("window_steps", ctypes.c_int32), ("deliver_lanes", ctypes.c_int32),
                 ("update_groups", ctypes.c_int32), ("l2_persist", ctypes.c_int32),
-                ("deliver_blocks", ctypes.c_int32)]
+                ("deliver_blocks", ctypes.c_int32), ("overlap", ctypes.c_int32)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)

@@ -483,6 +483,7 @@ static void default_launch(snn_net *h) {
   h->cfg.update_groups = 1;
   h->cfg.l2_persist = 1;
   h->cfg.deliver_blocks = 8;
+  h->cfg.overlap = 1;
 }
 
 extern "C" int snn_footprint(const snn_params *p, size_t *bytes_out) {
@@ -704,7 +705,8 @@ static int prepare_graphs(snn_net *h, uint32_t window) {
 // Capture the steps k = 0..steps-1 of a window starting at a step with
 // phase = t0 % nbuf: the update of every step, the delivery pass after every
 // step t with (t + 1) % kmin == 0.  With `ev`, event record nodes bracket every
-// kernel (ev[4k..4k+3]: update start/end, delivery start/end).
+// kernel (ev[4k..4k+3]: update start/end, delivery start/end) and the kernels
+// do not overlap.
 static int capture_steps(snn_net *h, const NetDev &d, uint32_t steps, uint32_t phase, const L2Window &l2,
                          cudaEvent_t *ev, cudaGraphExec_t *out, uint32_t *kernels) {
   const snn_launch &c = h->cfg;
@@ -712,16 +714,20 @@ static int capture_steps(snn_net *h, const NetDev &d, uint32_t steps, uint32_t p
   CU_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   cudaError_t err = cudaSuccess;
   uint32_t n = 0;
+  // programmatic dependent launch between the kernels, unless event nodes
+  // separate them (each kernel timed alone)
+  const bool pdl = c.overlap && !ev;
   for (uint32_t k = 0; k < steps && err == cudaSuccess; ++k) {
     if (ev) err = cudaEventRecordWithFlags(ev[4 * k + 0], cs, cudaEventRecordExternal);
-    const StepMod km{k % h->L.D, (phase + k) % h->L.nbuf};
-    if (err == cudaSuccess) err = launch_update(d, k, km, c.update_block, c.update_groups, l2, cs);
+    const uint32_t after_pass = (phase + k) % h->L.kmin == 0u;   // a pass followed step t0 + k - 1
+    const StepMod km{k % h->L.D, (phase + k) % h->L.nbuf, (!pdl || k == 0 || after_pass) ? 1u : 0u};
+    if (err == cudaSuccess) err = launch_update(d, k, km, c.update_block, c.update_groups, l2, pdl, cs);
     ++n;
     if (ev && err == cudaSuccess) err = cudaEventRecordWithFlags(ev[4 * k + 1], cs, cudaEventRecordExternal);
     if ((phase + k + 1u) % h->L.kmin == 0u) {
       if (ev && err == cudaSuccess) err = cudaEventRecordWithFlags(ev[4 * k + 2], cs, cudaEventRecordExternal);
       if (err == cudaSuccess)
-        err = launch_deliver(d, k, km, (uint32_t)c.deliver_lanes, c.deliver_warps, deliver_grid(h), l2, cs);
+        err = launch_deliver(d, k, km, (uint32_t)c.deliver_lanes, c.deliver_warps, deliver_grid(h), l2, pdl, cs);
       ++n;
       if (ev && err == cudaSuccess) err = cudaEventRecordWithFlags(ev[4 * k + 3], cs, cudaEventRecordExternal);
     }
@@ -1517,6 +1523,7 @@ extern "C" int snn_set_launch(snn_handle h, const snn_launch *cfg) {
     return fail(SNN_ERR_ARG, "update_groups 4 needs update_block <= 256");
   if (c.l2_persist != 0 && c.l2_persist != 1) return fail(SNN_ERR_ARG, "l2_persist must be 0 or 1");
   if (c.deliver_blocks < 1 || c.deliver_blocks > 32) return fail(SNN_ERR_ARG, "deliver_blocks must be in 1..32");
+  if (c.overlap != 0 && c.overlap != 1) return fail(SNN_ERR_ARG, "overlap must be 0 or 1");
   h->cfg = c;
   return SNN_OK;
 }
@@ -1634,12 +1641,13 @@ static int autotune_impl(snn_net *h, uint32_t trial_steps, int path_only) {
         }
     run_cands();
   }
-  if (status == SNN_OK && best.path == 0) {
-    // the L2 residency switch on the best shape: both settings timed again,
-    // and the persisting window is dropped only when that is clearly faster
+  // on/off switches on the best shape (the persisting L2 window, then the
+  // overlap of the kernels): both settings timed again, and a switch is
+  // turned off only when that is clearly faster
+  auto switch_trial = [&](int32_t snn_launch::*field) {
     snn_launch on = best, off = best;
-    on.l2_persist = 1;
-    off.l2_persist = 0;
+    on.*field = 1;
+    off.*field = 0;
     float ms_on = 0, ms_off = 0;
     status = trial(on, 3, &ms_on);
     if (status == SNN_OK) status = trial(off, 3, &ms_off);
@@ -1648,7 +1656,9 @@ static int autotune_impl(snn_net *h, uint32_t trial_steps, int path_only) {
       best = use_off ? off : on;
       best_ms = use_off ? ms_off : ms_on;
     }
-  }
+  };
+  if (status == SNN_OK && best.path == 0) switch_trial(&snn_launch::l2_persist);
+  if (status == SNN_OK && best.path == 0) switch_trial(&snn_launch::overlap);
   if (status == SNN_OK && !(best_ms < 0.97f * orig_ms)) best = orig;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -36,6 +36,8 @@ struct alignas(16) NetWin {
 struct StepMod {
   uint32_t slot;        // k mod D
   uint32_t buf;         // (t0 + k) mod nbuf
+  uint32_t state_ready; // update of step t0 + k: the previous step's state is final when the kernel starts
+                        // (the window's first step, or the previous kernel is a delivery pass)
 };
 
 // Recording header of a network (device memory, zeroed at every window start).
@@ -132,10 +134,11 @@ struct L2Window {
   size_t bytes = 0;
   float hit_ratio = 0.0f;
 };
+// pdl: launched with programmatic stream serialization (overlaps the previous kernel).
 cudaError_t launch_update(const NetDev &nd, uint32_t k, StepMod km, int block, int groups, const L2Window &l2,
-                          cudaStream_t s);
+                          bool pdl, cudaStream_t s);
 cudaError_t launch_deliver(const NetDev &nd, uint32_t k, StepMod km, uint32_t lanes, int warps, int blocks,
-                           const L2Window &l2, cudaStream_t s);
+                           const L2Window &l2, bool pdl, cudaStream_t s);
 cudaError_t launch_fused(const FusedTable &tab, uint32_t k, int block, int blocks, cudaStream_t s);
 int fused_blocks_per_sm(int block);   // resident fused blocks per SM
 // u16 entries per row of the delay-group table

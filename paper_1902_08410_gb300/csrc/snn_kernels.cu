@@ -94,24 +94,27 @@ __device__ __forceinline__ void red_add_u64(unsigned long long *addr, unsigned l
   asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(addr), "l"(v) : "memory");
 }
 
-// Loads that bypass L1 (streamed state), keeping L1 for the amplitude table.
-__device__ __forceinline__ float4 ld_na_f4(const float4 *p) {
+// L2-only loads (never served from L1) of data that other kernels of the
+// stream write: the neuron state and input buffers, and the spike lists and
+// counts, which the update of a step appends to while an overlapping delivery
+// pass reads older slots of the same arrays.  L1 stays for the amplitude table.
+__device__ __forceinline__ float4 ld_cg_f4(const float4 *p) {
   float4 v;
-  asm volatile("ld.global.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+  asm volatile("ld.global.cg.v4.f32 {%0, %1, %2, %3}, [%4];"
                : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
                : "l"(p));
   return v;
 }
-__device__ __forceinline__ int4 ld_na_i4(const int4 *p) {
+__device__ __forceinline__ int4 ld_cg_i4(const int4 *p) {
   int4 v;
-  asm volatile("ld.global.L1::no_allocate.v4.s32 {%0, %1, %2, %3}, [%4];"
+  asm volatile("ld.global.cg.v4.s32 {%0, %1, %2, %3}, [%4];"
                : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
                : "l"(p));
   return v;
 }
-__device__ __forceinline__ uint32_t ld_na_u32(const uint32_t *p) {
+__device__ __forceinline__ uint32_t ld_cg_u32(const uint32_t *p) {
   uint32_t v;
-  asm volatile("ld.global.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(v) : "l"(p));
   return v;
 }
 // Read-only loads of synapse records, not kept in L1 (each is used once).
@@ -257,24 +260,23 @@ struct Group4 {
 
 __device__ __forceinline__ void load_state4(const NetDev &nd, uint32_t n0, Group4 &g) {
   const uint32_t i4 = n0 >> 2;
-  g.V = ld_na_f4(reinterpret_cast<const float4 *>(nd.V) + i4);
-  g.c = ld_na_f4(reinterpret_cast<const float4 *>(nd.c) + i4);
-  g.ref = ld_na_u32(reinterpret_cast<const uint32_t *>(nd.ref) + i4);
+  g.V = ld_cg_f4(reinterpret_cast<const float4 *>(nd.V) + i4);
+  g.c = ld_cg_f4(reinterpret_cast<const float4 *>(nd.c) + i4);
+  g.ref = ld_cg_u32(reinterpret_cast<const uint32_t *>(nd.ref) + i4);
 }
 
-// Input buffer of the step (buffer `buf` = t % nbuf).  It is cleared by step4
+// Input buffer of the step (buffer `buf` = t % nbuf).  It is cleared by integrate4
 // after the neuron state is stored: a store right behind the load to the same
 // address held every later load of the warp back.
 __device__ __forceinline__ void load_input4(const NetDev &nd, uint32_t n0, uint32_t buf, Group4 &g) {
-  g.I = ld_na_i4(reinterpret_cast<const int4 *>(nd.acc + (size_t)buf * nd.N_pad) + (n0 >> 2));
+  g.I = ld_cg_i4(reinterpret_cast<const int4 *>(nd.acc + (size_t)buf * nd.N_pad) + (n0 >> 2));
 }
 
-// Advance the 4 neurons of g by step t (input buffers `buf`, read by
-// load_input4); returns the 4-bit spike mask and adds the number of external
-// events to n_ext.
-__device__ __forceinline__ uint32_t step4(const NetDev &nd, uint32_t n0, uint32_t t, uint32_t buf, Group4 &g,
-                                          uint32_t &n_ext) {
-  // one counter-based draw serves the four neurons (word n mod 4 each)
+// External drive of 4 neurons at step t (Poisson counts from one
+// counter-based draw, word n mod 4 each; amplitudes from the table): adds the
+// drive to I and the number of external events of the live neurons to n_ext.
+// Reads only the parameters and the amplitude table.
+__device__ __forceinline__ void drive4(const NetDev &nd, uint32_t n0, uint32_t t, int32_t (&I)[4], uint32_t &n_ext) {
   const uint4 R = philox4x32_10(n0 >> 2, t, 1u, 0u, nd.key0, nd.key1);
   const uint32_t Wv[4] = {R.x, R.y, R.z, R.w};
   uint32_t local = n0 % (uint32_t)kK;
@@ -286,21 +288,31 @@ __device__ __forceinline__ uint32_t step4(const NetDev &nd, uint32_t n0, uint32_
     kx[q] = poisson_count(nd, pops[q], Wv[q]);
     local = (local + 1u == (uint32_t)kK) ? 0u : local + 1u;
   }
-  int32_t Iv[4] = {g.I.x, g.I.y, g.I.z, g.I.w};
 #pragma unroll
   for (int q = 0; q < 4; ++q)   // first external event: independent table loads
-    if (kx[q]) Iv[q] += __ldg(nd.amp + pops[q] * kZTab + (Wv[q] & 0xFFFu));
-  extra_events_warp(nd, n0, t, kx, Iv);
+    if (kx[q]) I[q] += __ldg(nd.amp + pops[q] * kZTab + (Wv[q] & 0xFFFu));
+  extra_events_warp(nd, n0, t, kx, I);
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (n0 + q < nd.N) n_ext += kx[q];
+}
+
+// Advance the 4 neurons of g by one step (Eq. 2) with total input I (the
+// external drive plus the buffer g.I), store the state and clear input buffer
+// `buf`; returns the 4-bit spike mask.  Integer input: the order in which the
+// drive and the buffer are summed does not change the result.
+__device__ __forceinline__ uint32_t integrate4(const NetDev &nd, uint32_t n0, uint32_t buf, const Group4 &g,
+                                               const int32_t (&I)[4]) {
+  const int32_t Iv[4] = {I[0] + g.I.x, I[1] + g.I.y, I[2] + g.I.z, I[3] + g.I.w};
   float Vv[4] = {g.V.x, g.V.y, g.V.z, g.V.w};
   float cv[4] = {g.c.x, g.c.y, g.c.z, g.c.w};
   uint32_t rv[4] = {g.ref & 0xFFu, (g.ref >> 8) & 0xFFu, (g.ref >> 16) & 0xFFu, g.ref >> 24};
   uint32_t mask = 0;
+  uint32_t local = n0 % (uint32_t)kK;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    if (n0 + q < nd.N) {
-      n_ext += kx[q];
-      if (neuron_step(nd, pops[q], Vv[q], cv[q], rv[q], Iv[q])) mask |= 1u << q;
-    }
+    if (n0 + q < nd.N && neuron_step(nd, pop_of_local(local), Vv[q], cv[q], rv[q], Iv[q])) mask |= 1u << q;
+    local = (local + 1u == (uint32_t)kK) ? 0u : local + 1u;
   }
   if (n0 < nd.N) {
     const uint32_t i4 = n0 >> 2;
@@ -312,11 +324,15 @@ __device__ __forceinline__ uint32_t step4(const NetDev &nd, uint32_t n0, uint32_
   return mask;
 }
 
+// One step of 4 neurons: the state and input loads are issued first and are
+// in flight while the drive is computed.
 __device__ __forceinline__ uint32_t update4(const NetDev &nd, uint32_t n0, uint32_t t, uint32_t buf, uint32_t &n_ext) {
   Group4 g;
   load_state4(nd, n0, g);
   load_input4(nd, n0, buf, g);
-  return step4(nd, n0, t, buf, g, n_ext);
+  int32_t I[4] = {0, 0, 0, 0};
+  drive4(nd, n0, t, I, n_ext);
+  return integrate4(nd, n0, buf, g, I);
 }
 
 // Slot (t mod D) of step t = t0 + k from the window's residue and the step's,
@@ -422,7 +438,7 @@ __device__ __forceinline__ void warp_prefix(const NetDev &nd, uint32_t *pre, uin
   for (uint32_t base = 0; base < dmax; base += 32u) {
     const uint32_t d = base + lane + 1u;
     const bool use = d >= kmin && d <= dmax && !(skip_current && d == j + 1u);
-    uint32_t incl = use ? nd.cnt[slot_back(Tm, d, D)] : 0u;
+    uint32_t incl = use ? ld_cg_u32(nd.cnt + slot_back(Tm, d, D)) : 0u;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
@@ -490,7 +506,7 @@ __device__ __forceinline__ void deliver_segments(const NetDev &nd, const uint32_
       if (pre[mid] > g) hi = mid; else lo = mid + 1u;
     }
     const uint32_t d = lo, i = g - pre[d - 1u];
-    const uint32_t s = nd.hist[(size_t)slot_back(Tm, d, D) * nd.N_pad + i];
+    const uint32_t s = ld_cg_u32(nd.hist + (size_t)slot_back(Tm, d, D) * nd.N_pad + i);
     const uint16_t *o = nd.offs + (size_t)s * nd.os;
     const uint32_t a = o[d - 1u], b = o[d];
     if (sub == 0) prefetch_next_group(nd, s, o, d, b);   // read at a later pass
@@ -753,8 +769,13 @@ __global__ void __launch_bounds__(kBuildWarpsMax * 32) k_build_rows(const __grid
 // ---------------------------------------------------------------------------
 // Each thread advances G groups of 4 neurons; group g of block b covers the
 // neuron range ((b * G + g) * BLOCK + thread) * 4, so every warp owns whole
-// aligned 128-neuron tiles.  The state loads of all groups are issued before
-// the window is read, then the input buffers once the step is known.
+// aligned 128-neuron tiles.
+// Launched with programmatic dependent launch after the previous kernel of the
+// stream: the external drive (which reads no state) and, when the previous
+// kernel is a delivery pass (km.state_ready: that pass had waited for the
+// previous update), the neuron state are loaded before griddepcontrol.wait;
+// the input buffer, written by the passes, after it.  The trigger that follows
+// the wait lets the delivery pass after this step start on older spikes.
 // One group per thread is capped at 48 registers (40 resident warps per SM), so
 // that a 720k-neuron grid (37 warps per SM) runs in a single wave.
 template <int BLOCK, int G>
@@ -771,24 +792,38 @@ __global__ void __launch_bounds__(BLOCK, G == 1 ? 1280 / BLOCK : 1) k_update(con
     any |= live[g];
   }
   if (!any) return;
-  Group4 st4[G];
-#pragma unroll
-  for (int g = 0; g < G; ++g)
-    if (live[g]) {   // the state and the step's input buffer, before the window is read
-      load_state4(nd, n0[g], st4[g]);
-      load_input4(nd, n0[g], km.buf, st4[g]);
-    }
-  const NetWin w = *nd.win;
+  const NetWin w = *nd.win;   // written before the window's first kernel
   const uint32_t t = w.t0 + k;
   if (t >= w.t_end) return;
+  Group4 st4[G];
+  if (km.state_ready) {
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+      if (live[g]) load_state4(nd, n0[g], st4[g]);
+  }
+  int32_t I[G][4];
+  uint32_t n_ext[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    I[g][0] = I[g][1] = I[g][2] = I[g][3] = 0;
+    n_ext[g] = 0;
+    if (live[g]) drive4(nd, n0[g], t, I[g], n_ext[g]);
+  }
+  pdl_wait();      // the previous kernel (and everything before it) is complete
+  pdl_trigger();
   const uint32_t slot = step_slot(nd, w, km), buf = km.buf;
-  uint32_t mask[G], n_ext[G];
+  uint32_t mask[G];
 #pragma unroll
   for (int g = 0; g < G; ++g) {
     mask[g] = 0;
-    n_ext[g] = 0;
-    if (live[g]) mask[g] = step4(nd, n0[g], t, buf, st4[g], n_ext[g]);
+    if (live[g]) {
+      if (!km.state_ready) load_state4(nd, n0[g], st4[g]);
+      load_input4(nd, n0[g], buf, st4[g]);
+    }
   }
+#pragma unroll
+  for (int g = 0; g < G; ++g)
+    if (live[g]) mask[g] = integrate4(nd, n0[g], buf, st4[g], I[g]);
   // record per group whose tile is live (warp-uniform)
   if (live[G - 1]) {
     record_warp<G>(nd, mask, n0, n_ext, t, slot, k, w.bin0, nullptr, nullptr);
@@ -804,30 +839,56 @@ __global__ void __launch_bounds__(BLOCK, G == 1 ? 1280 / BLOCK : 1) k_update(con
 }
 
 // ---------------------------------------------------------------------------
-// Kernel: delivery pass after step t (two-kernel path; the update kernel of
-// step t has completed the step's spike list).  Every warp takes segments of
-// every target step of the pass.
+// Kernel: delivery pass after step t (two-kernel path).  Every warp takes
+// segments of every target step of the pass.  Launched with programmatic
+// dependent launch after the update of step t: the segments of older spikes
+// (steps before t, complete before that update started) are delivered first,
+// while the update may still run; after griddepcontrol.wait the step's own
+// spikes (their delay-kmin group, into the input of step t + kmin).  The
+// trigger after the wait lets the next update load its state and compute its
+// drive while the pass finishes.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(512, 2) k_deliver(const __grid_constant__ NetDev nd, uint32_t k, StepMod km,
                                                   uint32_t lanes) {
   __shared__ uint32_t s_pre[16][kPreLen];
-  const NetWin w = *nd.win;   // launched after the last step of an exchange period
+  const NetWin w = *nd.win;   // written before the window's first kernel
   const uint32_t t = w.t0 + k;
   if (t >= w.t_end) return;
   const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
   const uint32_t gpw = 32u / lanes, grp = lane / lanes, sub = lane % lanes;
   const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
   const uint32_t gw = blockIdx.x * (blockDim.x >> 5) + warp;
+  const uint32_t first = gw * gpw + grp, stride = nwarps * gpw;
   const uint32_t tm = step_slot(nd, w, km), tb = km.buf;
   uint32_t *pre = s_pre[warp];   // each warp its own prefix: no block barrier
   for (uint32_t j = 0; j < nd.kmin; ++j) {
     uint32_t Tm;
     int32_t *acc_T;
     target_of(nd, tm, tb, j, Tm, acc_T);
-    warp_prefix(nd, pre, Tm, j, false);
+    warp_prefix(nd, pre, Tm, j, true);
     __syncwarp();
-    deliver_segments(nd, pre, Tm, acc_T, pre[kPreLen - 1], gw * gpw + grp, nwarps * gpw, sub, lanes);
+    deliver_segments(nd, pre, Tm, acc_T, pre[kPreLen - 1], first, stride, sub, lanes);
     __syncwarp();   // every lane is done with the prefix before the next one
+  }
+  pdl_wait();       // the update of step t is complete: its spike list is final
+  pdl_trigger();
+  {
+    const uint32_t kmin = nd.kmin;
+    uint32_t Tm;
+    int32_t *acc_T;
+    target_of(nd, tm, tb, kmin - 1u, Tm, acc_T);
+    const uint32_t *ids = nd.hist + (size_t)tm * nd.N_pad;
+    // the list's first entry of this group is loaded together with the count
+    // (entries past the count are stale ids, in bounds and unused)
+    const uint32_t s0 = first < nd.N_pad ? ld_cg_u32(ids + first) : 0u;
+    const uint32_t n = ld_cg_u32(nd.cnt + tm);
+    for (uint32_t i = first; i < n; i += stride) {
+      const uint32_t s = i == first ? s0 : ld_cg_u32(ids + i);
+      const uint16_t *o = nd.offs + (size_t)s * nd.os;
+      const uint32_t a = o[kmin - 1u], b = o[kmin];
+      if (sub == 0) prefetch_next_group(nd, s, o, kmin, b);
+      add_records(nd, acc_T, s, a, b, sub, lanes);
+    }
   }
   if (blockIdx.x == 0) clear_next_counts(nd, t);
 }
@@ -962,16 +1023,24 @@ cudaError_t launch_build_rows(const NetDev &h_nd, const BuildDev &bd, cudaStream
 }
 
 // Launch with an optional persisting L2 access-policy window.
+// Launch with an optional persisting L2 access-policy window and, with `pdl`,
+// programmatic stream serialization (the kernel may start once every block of
+// the previous kernel has passed griddepcontrol.launch_dependents).
 template <typename... Args>
 static cudaError_t launch_ex(void (*kernel)(Args...), dim3 grid, dim3 block, size_t smem, const L2Window &l2,
-                             cudaStream_t s, Args... args) {
+                             bool pdl, cudaStream_t s, Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   unsigned n = 0;
+  if (pdl) {
+    attr[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[n].val.programmaticStreamSerializationAllowed = 1;
+    ++n;
+  }
   if (l2.bytes) {
     attr[n].id = cudaLaunchAttributeAccessPolicyWindow;
     attr[n].val.accessPolicyWindow.base_ptr = l2.base;
@@ -987,11 +1056,11 @@ static cudaError_t launch_ex(void (*kernel)(Args...), dim3 grid, dim3 block, siz
 }
 
 cudaError_t launch_update(const NetDev &nd, uint32_t k, StepMod km, int block, int groups, const L2Window &l2,
-                          cudaStream_t s) {
+                          bool pdl, cudaStream_t s) {
   const uint32_t per_block = (uint32_t)block * 4u * (uint32_t)groups;
   const uint32_t blocks = (nd.N_pad + per_block - 1) / per_block;
 #define SNN_UPD(B, G) \
-  if (block == B && groups == G) return launch_ex(k_update<B, G>, dim3(blocks), dim3(B), 0, l2, s, nd, k, km);
+  if (block == B && groups == G) return launch_ex(k_update<B, G>, dim3(blocks), dim3(B), 0, l2, pdl, s, nd, k, km);
   SNN_UPD(64, 1) SNN_UPD(128, 1) SNN_UPD(128, 2) SNN_UPD(128, 4)
   SNN_UPD(256, 1) SNN_UPD(256, 2) SNN_UPD(256, 4)
   SNN_UPD(512, 1) SNN_UPD(512, 2)
@@ -1000,9 +1069,9 @@ cudaError_t launch_update(const NetDev &nd, uint32_t k, StepMod km, int block, i
 }
 
 cudaError_t launch_deliver(const NetDev &nd, uint32_t k, StepMod km, uint32_t lanes, int warps, int blocks,
-                           const L2Window &l2, cudaStream_t s) {
+                           const L2Window &l2, bool pdl, cudaStream_t s) {
   if (warps < 1 || warps > 16 || blocks < 1 || !valid_lanes(lanes)) return cudaErrorInvalidValue;
-  return launch_ex(k_deliver, dim3((unsigned)blocks), dim3(warps * 32), 0, l2, s, nd, k, km, lanes);
+  return launch_ex(k_deliver, dim3((unsigned)blocks), dim3(warps * 32), 0, l2, pdl, s, nd, k, km, lanes);
 }
 
 cudaError_t launch_fused(const FusedTable &tab, uint32_t k, int block, int blocks, cudaStream_t s) {

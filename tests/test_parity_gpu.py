@@ -283,6 +283,10 @@ def test_launch_shapes_and_autotune_keep_results(snn, oracle_mod):
                    deliver_blocks=16),
               dict(path=0, update_block=128, update_groups=2, deliver_warps=8, window_steps=70, deliver_lanes=4,
                    deliver_blocks=1, l2_persist=0),
+              dict(path=0, update_block=128, update_groups=1, deliver_warps=4, window_steps=45, deliver_lanes=8,
+                   overlap=0),
+              dict(path=0, update_block=512, update_groups=1, deliver_warps=16, window_steps=97, deliver_lanes=16,
+                   deliver_blocks=32, overlap=1),
               dict(path=1, fused_block=128, fused_items_per_sm=1, window_steps=64, deliver_lanes=8),
               dict(path=1, fused_block=512, fused_items_per_sm=4, window_steps=128, deliver_lanes=4),
               dict(path=1, fused_block=128, fused_items_per_sm=16, window_steps=300, deliver_lanes=32)]
