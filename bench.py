@@ -87,6 +87,8 @@ def parse_args():
     ap.add_argument("--deliver-blocks", type=int, default=8)
     ap.add_argument("--l2-persist", type=int, choices=[0, 1], default=1,
                     help="persisting L2 window (profile mode, and grid mode with --no-tune)")
+    ap.add_argument("--overlap", type=int, choices=[0, 1], default=1,
+                    help="profile mode: kernels of consecutive steps overlap (programmatic dependent launch)")
     ap.add_argument("--grid64-lambdas", type=str, default="0.4,1.0,2.0")
     ap.add_argument("--batch-nets", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=20_000)
@@ -971,7 +973,7 @@ def run_profile_mode(args, dist: Dist):
     net.launch = {"path": args.path, "window_steps": args.window, "update_block": args.update_block,
                   "update_groups": args.update_groups, "deliver_warps": args.deliver_warps,
                   "deliver_lanes": args.deliver_lanes, "l2_persist": args.l2_persist,
-                  "deliver_blocks": args.deliver_blocks}
+                  "deliver_blocks": args.deliver_blocks, "overlap": args.overlap}
     net.run(args.warm_steps)
     net.run(args.run_steps)
     torch.cuda.synchronize()

@@ -984,7 +984,7 @@ struct BatchCtx {
   cudaStream_t cap_stream = nullptr, copy_stream = nullptr;
   cudaEvent_t ev_block[2] = {nullptr, nullptr};
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
-  uint32_t exec_window = 0, exec_items = 0, exec_lanes = 0;
+  uint32_t exec_window = 0, exec_items = 0, exec_lanes = 0, exec_chunks = 0;
   uint32_t pinned_count = 0;   // staging of the item count (copied before the replays)
   int exec_block = 0, exec_blocks = 0;
   void drop_graphs() {
@@ -1087,15 +1087,18 @@ static int run_fused(snn_net *const *hs, const uint64_t *steps, int32_t n) {
       d.win = static_cast<const NetWin *>(B.wins[b].p) + i;
       B.pinned_nets[(size_t)b * B.cap + i] = d;
     }
+  uint32_t max_delay = 1;
+  for (int i = 0; i < n; ++i) max_delay = std::max<uint32_t>(max_delay, (uint32_t)hs[i]->p.n_delay);
+  const uint32_t chunks = pre_chunks(max_delay);   // delay chunks of the largest delay in the batch
   const int sms = hs[0]->sm_count > 0 ? hs[0]->sm_count : 148;
-  const int per_sm = std::min(cfg.fused_items_per_sm, fused_blocks_per_sm(block));
+  const int per_sm = std::min(cfg.fused_items_per_sm, fused_blocks_per_sm(block, chunks));
   const int blocks = sms * per_sm;   // fixed grid: the same graphs serve any set of networks
   if (!B.exec[0] || !B.exec[1] || B.exec_window != window || B.exec_block != block || B.exec_blocks != blocks ||
-      B.exec_lanes != lanes) {
+      B.exec_lanes != lanes || B.exec_chunks != chunks) {
     B.drop_graphs();
     for (int b = 0; b < 2; ++b) {
       FusedTable tab{static_cast<const NetDev *>(B.nets[b].p), static_cast<const FusedItem *>(B.items.p),
-                     static_cast<const uint32_t *>(B.n_items_dev.p), lanes};
+                     static_cast<const uint32_t *>(B.n_items_dev.p), lanes, chunks};
       CU_TRY(cudaStreamBeginCapture(B.cap_stream, cudaStreamCaptureModeThreadLocal));
       cudaError_t err = cudaSuccess;
       for (uint32_t k = 0; k < window && err == cudaSuccess; ++k)
@@ -1116,6 +1119,7 @@ static int run_fused(snn_net *const *hs, const uint64_t *steps, int32_t n) {
     B.exec_block = block;
     B.exec_blocks = blocks;
     B.exec_lanes = lanes;
+    B.exec_chunks = chunks;
   }
   CU_TRY(cudaMemcpyAsync(B.items.p, B.pinned_items, n_items * sizeof(FusedItem), cudaMemcpyHostToDevice, s));
   B.pinned_count = (uint32_t)n_items;

@@ -122,6 +122,7 @@ struct FusedTable {
   const FusedItem *items;
   const uint32_t *n_items;  // item count in device memory (the graph outlives any one batch)
   uint32_t lanes;           // lanes per delivery segment
+  uint32_t chunks;          // register prefix chunks of 32 delays: 1 or kMaxPreChunks (largest n_delay of the table)
 };
 
 // ---- launchers (snn_kernels.cu) -------------------------------------------
@@ -140,7 +141,11 @@ cudaError_t launch_update(const NetDev &nd, uint32_t k, StepMod km, int block, i
 cudaError_t launch_deliver(const NetDev &nd, uint32_t k, StepMod km, uint32_t lanes, int warps, int blocks,
                            const L2Window &l2, bool pdl, cudaStream_t s);
 cudaError_t launch_fused(const FusedTable &tab, uint32_t k, int block, int blocks, cudaStream_t s);
-int fused_blocks_per_sm(int block);   // resident fused blocks per SM
+int fused_blocks_per_sm(int block, uint32_t chunks);   // resident fused blocks per SM
+// Delivery keeps each warp's segment prefix in registers, in chunks of 32
+// delays: one chunk up to n_delay 32, else kMaxPreChunks (n_delay <= 256).
+constexpr uint32_t kMaxPreChunks = 8;
+inline uint32_t pre_chunks(uint32_t n_delay) { return n_delay <= 32u ? 1u : kMaxPreChunks; }
 // u16 entries per row of the delay-group table
 inline uint32_t offs_stride(uint32_t n_delay) { return (n_delay + 1u + 7u) & ~7u; }
 int device_sm_count();

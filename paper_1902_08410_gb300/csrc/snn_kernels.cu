@@ -23,10 +23,11 @@
 // step equals the minimum delay): it produces the inputs of steps t + 1 ..
 // t + kmin, for each of them adding, for d = kmin..n_delay, the delay-d group
 // of every spike of step T - d.  Every record handled lands in one of the
-// next kmin steps, so the input is kmin + 1 int32 buffers per neuron (the one
-// being read is never written; they stay in L2) instead of a ring of
-// n_delay + 1 slots.  The spikes of the last n_delay + kmin steps are kept per
-// step slot in `hist`.
+// next kmin steps, so the input needs only kmin + 1 int32 buffers per neuron
+// (the one being read is never written); 2 kmin are kept, so that windows
+// starting at the same step mod 2 kmin share one captured graph, instead of a
+// ring of n_delay + 1 slots.  They stay in L2.  The spikes of the last
+// n_delay + kmin steps are kept per step slot in `hist`.
 #include <algorithm>
 #include <cstdint>
 
@@ -421,36 +422,73 @@ __device__ __forceinline__ void record_warp(const NetDev &nd, const uint32_t (&m
 // spread over all warps of the grid, `lanes` lanes per segment, and their
 // records are reduced straight into the input buffer of T.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kPreLen = 264;   // per-warp segment prefix over delays (n_delay <= 254)
-
 // Slot of step T - d, Tm = T mod D, 1 <= d < D.
 __device__ __forceinline__ uint32_t slot_back(uint32_t Tm, uint32_t d, uint32_t D) { return Tm >= d ? Tm - d : Tm + D - d; }
 
-// One warp: pre[d] = spikes of steps T - d' summed over kmin <= d' <= d
-// (pre[d] = 0 below kmin), T = t + 1 + j with Tm = T mod D; the spikes of step
-// t itself are left out when skip_current.  pre[kPreLen - 1] = the total.
-// Lane l handles delay base + l + 1: one load and one scan per 32 delays.
-__device__ __forceinline__ void warp_prefix(const NetDev &nd, uint32_t *pre, uint32_t Tm, uint32_t j,
+// Segment prefix of one target step, held in registers across the warp:
+// lane l of chunk c stands for delay d = 32 c + l + 1, with incl[c] = the
+// spikes of steps T - d' summed over kmin <= d' <= d (0 below kmin; past
+// n_delay it stays at the total) and base[c] = the sum below the chunk.
+// NCH = chunks of 32 delays (n_delay <= 32 NCH).  No shared memory.
+template <int NCH>
+struct WarpPrefix {
+  uint32_t incl[NCH];
+  uint32_t base[NCH];
+  uint32_t total;
+};
+
+// T = t + 1 + j with Tm = T mod D; the spikes of step t itself are left out
+// when skip_current.  The count loads of all chunks are issued first.
+template <int NCH>
+__device__ __forceinline__ void warp_prefix(const NetDev &nd, WarpPrefix<NCH> &P, uint32_t Tm, uint32_t j,
                                             bool skip_current) {
   const uint32_t lane = lane_id();
   const uint32_t D = nd.D, dmax = nd.n_delay, kmin = nd.kmin;
-  uint32_t run = 0;
-  for (uint32_t base = 0; base < dmax; base += 32u) {
-    const uint32_t d = base + lane + 1u;
+  uint32_t v[NCH];
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    const uint32_t d = 32u * c + lane + 1u;
     const bool use = d >= kmin && d <= dmax && !(skip_current && d == j + 1u);
-    uint32_t incl = use ? ld_cg_u32(nd.cnt + slot_back(Tm, d, D)) : 0u;
+    v[c] = use ? ld_cg_u32(nd.cnt + slot_back(Tm, d, D)) : 0u;
+  }
+  uint32_t run = 0;
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    uint32_t x = v[c];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-      if (lane >= (uint32_t)o) incl += y;
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= (uint32_t)o) x += y;
     }
-    incl += run;
-    if (d <= dmax) pre[d] = incl;
-    run = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    P.base[c] = run;
+    P.incl[c] = x + run;
+    run = __shfl_sync(0xFFFFFFFFu, P.incl[c], 31);
   }
-  if (lane == 0) {
-    pre[0] = 0u;
-    pre[kPreLen - 1] = run;
+  P.total = run;
+}
+
+// The delay d of segment g of this lane's group (smallest d with prefix > g)
+// and the prefix below it; d = 0 when g >= the total.  Called by whole warps:
+// every group's g is tested against a chunk with one ballot.
+template <int NCH>
+__device__ __forceinline__ void find_delay(const WarpPrefix<NCH> &P, uint32_t g, uint32_t lanes, uint32_t &d,
+                                           uint32_t &below) {
+  const uint32_t lane = lane_id(), grp = lane / lanes, gpw = 32u / lanes;
+  d = 0;
+  below = 0;
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    uint32_t first = 32u;   // this group's first lane of the chunk with prefix > g
+    for (uint32_t q = 0; q < gpw; ++q) {
+      const uint32_t gq = __shfl_sync(0xFFFFFFFFu, g, q * lanes);
+      const uint32_t bal = __ballot_sync(0xFFFFFFFFu, P.incl[c] > gq);
+      if (grp == q && bal) first = (uint32_t)(__ffs(bal) - 1);
+    }
+    const uint32_t prev = __shfl_sync(0xFFFFFFFFu, P.incl[c], (first - 1u) & 31u);
+    if (d == 0 && first < 32u) {
+      d = 32u * c + first + 1u;
+      below = first ? prev : P.base[c];
+    }
   }
 }
 
@@ -493,20 +531,20 @@ __device__ __forceinline__ void add_records(const NetDev &nd, int32_t *acc_T, ui
   }
 }
 
-// Segments g = first, first + stride, ... < S of the target step with slot Tm
-// (prefix `pre` from warp_prefix), each by the `lanes` lanes of one group.
-__device__ __forceinline__ void deliver_segments(const NetDev &nd, const uint32_t *pre, uint32_t Tm, int32_t *acc_T,
-                                                 uint32_t S, uint32_t first, uint32_t stride, uint32_t sub,
-                                                 uint32_t lanes) {
-  const uint32_t D = nd.D, dmax = nd.n_delay;
-  for (uint32_t g = first; g < S; g += stride) {
-    uint32_t lo = 1u, hi = dmax;   // the segment's delay: smallest d with pre[d] > g
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (pre[mid] > g) hi = mid; else lo = mid + 1u;
-    }
-    const uint32_t d = lo, i = g - pre[d - 1u];
-    const uint32_t s = ld_cg_u32(nd.hist + (size_t)slot_back(Tm, d, D) * nd.N_pad + i);
+// Segments of the target step with slot Tm (prefix P): the warp takes
+// segments wbase .. wbase + 32 / lanes - 1, then the same plus stride, ...,
+// one per group of `lanes` lanes (this lane is `sub` of group grp).
+template <int NCH>
+__device__ __forceinline__ void deliver_segments(const NetDev &nd, const WarpPrefix<NCH> &P, uint32_t Tm,
+                                                 int32_t *acc_T, uint32_t wbase, uint32_t stride, uint32_t lanes) {
+  const uint32_t D = nd.D;
+  const uint32_t lane = lane_id(), grp = lane / lanes, sub = lane % lanes;
+  for (uint32_t gb = wbase; gb < P.total; gb += stride) {   // warp-uniform
+    const uint32_t g = gb + grp;
+    uint32_t d, below;
+    find_delay<NCH>(P, g, lanes, d, below);
+    if (d == 0) continue;   // g past the total (last round)
+    const uint32_t s = ld_cg_u32(nd.hist + (size_t)slot_back(Tm, d, D) * nd.N_pad + (g - below));
     const uint16_t *o = nd.offs + (size_t)s * nd.os;
     const uint32_t a = o[d - 1u], b = o[d];
     if (sub == 0) prefetch_next_group(nd, s, o, d, b);   // read at a later pass
@@ -848,9 +886,11 @@ __global__ void __launch_bounds__(BLOCK, G == 1 ? 1280 / BLOCK : 1) k_update(con
 // trigger after the wait lets the next update load its state and compute its
 // drive while the pass finishes.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(512, 2) k_deliver(const __grid_constant__ NetDev nd, uint32_t k, StepMod km,
+// One prefix chunk (n_delay <= 32) fits in 40 registers: three 512-thread
+// blocks per SM.
+template <int NCH>
+__global__ void __launch_bounds__(512, NCH == 1 ? 3 : 2) k_deliver(const __grid_constant__ NetDev nd, uint32_t k, StepMod km,
                                                   uint32_t lanes) {
-  __shared__ uint32_t s_pre[16][kPreLen];
   const NetWin w = *nd.win;   // written before the window's first kernel
   const uint32_t t = w.t0 + k;
   if (t >= w.t_end) return;
@@ -860,15 +900,13 @@ __global__ void __launch_bounds__(512, 2) k_deliver(const __grid_constant__ NetD
   const uint32_t gw = blockIdx.x * (blockDim.x >> 5) + warp;
   const uint32_t first = gw * gpw + grp, stride = nwarps * gpw;
   const uint32_t tm = step_slot(nd, w, km), tb = km.buf;
-  uint32_t *pre = s_pre[warp];   // each warp its own prefix: no block barrier
   for (uint32_t j = 0; j < nd.kmin; ++j) {
     uint32_t Tm;
     int32_t *acc_T;
     target_of(nd, tm, tb, j, Tm, acc_T);
-    warp_prefix(nd, pre, Tm, j, true);
-    __syncwarp();
-    deliver_segments(nd, pre, Tm, acc_T, pre[kPreLen - 1], first, stride, sub, lanes);
-    __syncwarp();   // every lane is done with the prefix before the next one
+    WarpPrefix<NCH> P;   // each warp its own prefix, in registers
+    warp_prefix<NCH>(nd, P, Tm, j, true);
+    deliver_segments<NCH>(nd, P, Tm, acc_T, gw * gpw, stride, lanes);
   }
   pdl_wait();       // the update of step t is complete: its spike list is final
   pdl_trigger();
@@ -897,17 +935,19 @@ __global__ void __launch_bounds__(512, 2) k_deliver(const __grid_constant__ NetD
 // Kernel: fused step over a table of networks.  A block takes work items
 // (network, 4*blockDim neurons): update and recording with a block-local spike
 // list and, after the last step of an exchange period, the delay-kmin records
-// of those spikes and the item's share of the rest of the network's pass.  Update reads input buffer t % nbuf and
-// delivery writes the buffers of steps t + 1 .. t + kmin (nbuf = kmin + 1:
-// never the one being read), so blocks need no grid-wide barrier; many small
-// blocks per SM let one block's update overlap another's delivery.  Launched with programmatic dependent launch: the
-// prologue (descriptor copy, window read) runs while the previous step drains.
+// of those spikes and the item's share of the rest of the network's pass.
+// Update reads input buffer t % nbuf and delivery writes the buffers of steps
+// t + 1 .. t + kmin (nbuf = 2 kmin > kmin: never the one being read), so
+// blocks need no grid-wide barrier; many small blocks per SM let one block's
+// update overlap another's delivery.  Launched with programmatic dependent
+// launch: the prologue (descriptor copy, window read) runs while the previous
+// step drains.
 // ---------------------------------------------------------------------------
+template <int NCH>
 __global__ void __launch_bounds__(512) k_fused(const __grid_constant__ FusedTable tab, uint32_t k) {
   extern __shared__ __align__(128) uint8_t smem[];   // the item's spike ids (4 * blockDim)
   __shared__ NetDev nd;
   __shared__ NetWin s_win;
-  __shared__ uint32_t s_pre[16][kPreLen];
   __shared__ uint32_t s_count;
   __shared__ uint32_t s_net;
   uint32_t *s_ids = reinterpret_cast<uint32_t *>(smem);
@@ -950,16 +990,14 @@ __global__ void __launch_bounds__(512) k_fused(const __grid_constant__ FusedTabl
       // the item's share of the pass: its network's segments are dealt over
       // all groups of all the network's items
       const uint32_t gpb = blockDim.x / lanes, gpw = 32u / lanes;
-      const uint32_t first = item.index * gpb + warp * gpw + lane / lanes, stride = item.count * gpb;
-      uint32_t *pre = s_pre[warp];
+      const uint32_t wbase = item.index * gpb + warp * gpw, stride = item.count * gpb;
       for (uint32_t j = 0; j < nd.kmin; ++j) {
         uint32_t Tm;
         int32_t *acc_T;
         target_of(nd, tm, tb, j, Tm, acc_T);
-        warp_prefix(nd, pre, Tm, j, true);
-        __syncwarp();
-        deliver_segments(nd, pre, Tm, acc_T, pre[kPreLen - 1], first, stride, lane % lanes, lanes);
-        __syncwarp();
+        WarpPrefix<NCH> P;
+        warp_prefix<NCH>(nd, P, Tm, j, true);
+        deliver_segments<NCH>(nd, P, Tm, acc_T, wbase, stride, lanes);
       }
       if (item.index == 0) clear_next_counts(nd, t);
     }
@@ -1071,7 +1109,12 @@ cudaError_t launch_update(const NetDev &nd, uint32_t k, StepMod km, int block, i
 cudaError_t launch_deliver(const NetDev &nd, uint32_t k, StepMod km, uint32_t lanes, int warps, int blocks,
                            const L2Window &l2, bool pdl, cudaStream_t s) {
   if (warps < 1 || warps > 16 || blocks < 1 || !valid_lanes(lanes)) return cudaErrorInvalidValue;
-  return launch_ex(k_deliver, dim3((unsigned)blocks), dim3(warps * 32), 0, l2, pdl, s, nd, k, km, lanes);
+  if (pre_chunks(nd.n_delay) == 1u)
+    return launch_ex(k_deliver<1>, dim3((unsigned)blocks), dim3(warps * 32), 0, l2, pdl, s, nd, k, km, lanes);
+  if (nd.n_delay <= 32u * kMaxPreChunks)
+    return launch_ex(k_deliver<kMaxPreChunks>, dim3((unsigned)blocks), dim3(warps * 32), 0, l2, pdl, s, nd, k, km,
+                     lanes);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_fused(const FusedTable &tab, uint32_t k, int block, int blocks, cudaStream_t s) {
@@ -1086,13 +1129,18 @@ cudaError_t launch_fused(const FusedTable &tab, uint32_t k, int block, int block
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_fused, tab, k);
+  if (tab.chunks == 1u) return cudaLaunchKernelEx(&cfg, k_fused<1>, tab, k);
+  if (tab.chunks == kMaxPreChunks) return cudaLaunchKernelEx(&cfg, k_fused<kMaxPreChunks>, tab, k);
+  return cudaErrorInvalidValue;
 }
 
-int fused_blocks_per_sm(int block) {
+int fused_blocks_per_sm(int block, uint32_t chunks) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused, block, fused_smem_bytes(block)) != cudaSuccess)
-    return 1;
+  cudaError_t e = chunks == 1u
+                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<1>, block, fused_smem_bytes(block))
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<kMaxPreChunks>, block,
+                                                                      fused_smem_bytes(block));
+  if (e != cudaSuccess) return 1;
   return n > 0 ? n : 1;
 }
 
