@@ -134,8 +134,9 @@ typedef void (*snn_free_fn)(void *ptr, void *ctx);
 int snn_set_allocator(snn_alloc_fn alloc, snn_free_fn free_fn, void *ctx);
 
 /* Device bytes a network with these parameters will hold once built
- * (synapse records and their delay-group table, neuron state, input buffers,
- * spike history of the last n_delay + 1 steps, tables, recording buffers). */
+ * (synapse records and their delay-group table, neuron state, 2 max(1, min_delay)
+ * input buffers, spike history of the last n_delay + max(1, min_delay) steps,
+ * tables, recording buffers). */
 int snn_footprint(const snn_params *p, size_t *bytes_out);
 
 /* Build a network on the device (Sec. 2.1 initialisation; Eq. 1 connectivity,
