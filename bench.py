@@ -80,11 +80,11 @@ def parse_args():
     ap.add_argument("--warm-steps", type=int, default=1024)
     ap.add_argument("--run-steps", type=int, default=64)
     ap.add_argument("--window", type=int, default=64)
-    ap.add_argument("--update-block", type=int, default=128)
+    ap.add_argument("--update-block", type=int, default=256)
     ap.add_argument("--update-groups", type=int, default=1)
-    ap.add_argument("--deliver-warps", type=int, default=4)
-    ap.add_argument("--deliver-lanes", type=int, default=8)
-    ap.add_argument("--deliver-blocks", type=int, default=8)
+    ap.add_argument("--deliver-warps", type=int, default=16)
+    ap.add_argument("--deliver-lanes", type=int, default=32)
+    ap.add_argument("--deliver-blocks", type=int, default=3)
     ap.add_argument("--l2-persist", type=int, choices=[0, 1], default=1,
                     help="persisting L2 window (profile mode, and grid mode with --no-tune)")
     ap.add_argument("--overlap", type=int, choices=[0, 1], default=1,
@@ -604,8 +604,8 @@ def run_gb300(args, dist: Dist):
             "config": {"workload": WORKLOAD, "networks_per_gpu": 2, "neurons_per_gpu": sum(n.N for n in nets),
                        "recurrent_synapses_per_gpu": sum(n.N * n.M for n in nets),
                        "sim_seconds_per_step_per_network": steps * W.DT_MS * 1e-3,
-                       "l2": "inputs larger than L2 (2 x 6.5 GB synapse records); the neuron state and delay ring "
-                             "of each network (~67 MB) stay in L2 across time steps by design",
+                       "l2": "inputs larger than L2 (2 x 6.5 GB synapse records); the neuron state and input "
+                             "buffers of each network (~12 MB) stay in L2 across time steps by design",
                        "launch": launch_cfgs, "parallelism": f"replicas x{dist.world}",
                        "networks_run": {"sequential": "one after the other",
                                         "concurrent": "concurrently, one CUDA stream each, two-kernel path "
@@ -919,8 +919,8 @@ def run_min_delay_mode(args, dist: Dist):
     """The paper's exchange step (Sec. 2.1.1): a 24x24 AW network with delays
     of 10..20 steps (minimum delay 1 ms), delivered once per 10 steps, beside
     the benchmark form with delays of 1..20 steps delivered every step.  Both
-    tuned after their first 5000 steps; events/s, time per step and kernel
-    launches per simulated millisecond."""
+    on the two-kernel path, tuned after their first 5000 steps; events/s, time
+    per step and kernel launches per simulated millisecond."""
     import torch
     torch.cuda.set_device(dist.local_rank)
     import paper_1902_08410_gb300 as snn
@@ -931,7 +931,7 @@ def run_min_delay_mode(args, dist: Dist):
         p["min_delay"] = kmin
         net = snn.Network(p, 1)
         net.run(5000)
-        cfg = net.autotune(300)
+        cfg = net.autotune(300, path=0)   # both forms on the two-kernel path: one pass launch per exchange
         st0 = net.stats()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         sampler = ClockSampler(gpu_selector(dist.local_rank))

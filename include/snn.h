@@ -233,7 +233,8 @@ int snn_autotune_path(snn_handle h, uint32_t trial_steps, int32_t path);
  * shape replaces the first network's current shape only if at least 3%
  * faster, and is set on every network with launch path 1.  The networks must
  * share one device; the call is ordered on the first network's stream.
- * Allocates a temporary copy of each network's neuron state and ring. */
+ * Allocates a temporary copy of each network's neuron state, input buffers and
+ * spike history. */
 int snn_autotune_batch(const snn_handle *hs, int32_t n, uint32_t trial_steps);
 
 /* Measure the two-kernel path on the next `steps` (1..window) steps, then
@@ -241,11 +242,13 @@ int snn_autotune_batch(const snn_handle *hs, int32_t n, uint32_t trial_steps);
  * network's stream: once captured into one CUDA graph as snn_run runs them
  * (ms_out[2] = mean time per step in milliseconds, CUDA events around the
  * graph; the state is then restored from a device snapshot), and once with an
- * event record node before and after every kernel (ms_out[0] / ms_out[1] =
+ * event record node before and after every kernel, each kernel then running
+ * alone, without the overlap of consecutive kernels (ms_out[0] / ms_out[1] =
  * mean span of one update / one delivery launch; event nodes lengthen each
  * span, so their ratio is the reliable part).  ms_out holds 3 doubles.
  * Results are identical to snn_run; the call exists to measure kernels without
- * a profiler.  Allocates a temporary copy of the neuron state and ring. */
+ * a profiler.  Allocates a temporary copy of the neuron state, input buffers
+ * and spike history. */
 int snn_time_kernels(snn_handle h, uint32_t steps, double *ms_out);
 
 /* Build the synapse rows of a network (the same construction and the same

@@ -36,8 +36,8 @@ struct alignas(16) NetWin {
 struct StepMod {
   uint32_t slot;        // k mod D
   uint32_t buf;         // (t0 + k) mod nbuf
-  uint32_t state_ready; // update of step t0 + k: the previous step's state is final when the kernel starts
-                        // (the window's first step, or the previous kernel is a delivery pass)
+  uint32_t overlapped;  // update of step t0 + k: launched to overlap the delivery pass before it
+                        // (programmatic dependent launch; its input buffer is read after griddepcontrol.wait)
 };
 
 // Recording header of a network (device memory, zeroed at every window start).

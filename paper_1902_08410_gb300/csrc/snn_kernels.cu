@@ -611,7 +611,7 @@ __global__ void k_init_state(const __grid_constant__ NetDev nd) {
 // uniform delay, Gaussian efficacy), each row ordered by key (delay << 24 |
 // target), records with equal keys in draw order: grouped by delay and sorted
 // by target within a delay, so that the lanes of one delivery instruction
-// often update the same 32-byte sector of the ring.
+// often update the same 32-byte sector of the input buffer.
 // Grid (G, 5): block (m, y) builds rows of module m, local indices
 // [250 y, 250 y + 250).  One warp per row at a time.  A warp keeps, per draw,
 // the key and the 12-bit quantile index of its efficacy (the weight is formed
@@ -808,12 +808,14 @@ __global__ void __launch_bounds__(kBuildWarpsMax * 32) k_build_rows(const __grid
 // Each thread advances G groups of 4 neurons; group g of block b covers the
 // neuron range ((b * G + g) * BLOCK + thread) * 4, so every warp owns whole
 // aligned 128-neuron tiles.
-// Launched with programmatic dependent launch after the previous kernel of the
-// stream: the external drive (which reads no state) and, when the previous
-// kernel is a delivery pass (km.state_ready: that pass had waited for the
-// previous update), the neuron state are loaded before griddepcontrol.wait;
-// the input buffer, written by the passes, after it.  The trigger that follows
-// the wait lets the delivery pass after this step start on older spikes.
+// The neuron state is final when the kernel starts: either the kernel before
+// it has finished, or (km.overlapped) it is a delivery pass launched after the
+// previous update, which it waited for before letting this kernel start.  The
+// state loads are issued first, then the external drive (which reads no state)
+// is computed; without overlap the input buffer is loaded with the state, with
+// it only after griddepcontrol.wait (the pass writes that buffer).  The trigger
+// that follows the wait lets the delivery pass after this step start on older
+// spikes.
 // One group per thread is capped at 48 registers (40 resident warps per SM), so
 // that a 720k-neuron grid (37 warps per SM) runs in a single wave.
 template <int BLOCK, int G>
@@ -834,11 +836,12 @@ __global__ void __launch_bounds__(BLOCK, G == 1 ? 1280 / BLOCK : 1) k_update(con
   const uint32_t t = w.t0 + k;
   if (t >= w.t_end) return;
   Group4 st4[G];
-  if (km.state_ready) {
 #pragma unroll
-    for (int g = 0; g < G; ++g)
-      if (live[g]) load_state4(nd, n0[g], st4[g]);
-  }
+  for (int g = 0; g < G; ++g)
+    if (live[g]) {
+      load_state4(nd, n0[g], st4[g]);
+      if (!km.overlapped) load_input4(nd, n0[g], km.buf, st4[g]);
+    }
   int32_t I[G][4];
   uint32_t n_ext[G];
 #pragma unroll
@@ -854,10 +857,7 @@ __global__ void __launch_bounds__(BLOCK, G == 1 ? 1280 / BLOCK : 1) k_update(con
 #pragma unroll
   for (int g = 0; g < G; ++g) {
     mask[g] = 0;
-    if (live[g]) {
-      if (!km.state_ready) load_state4(nd, n0[g], st4[g]);
-      load_input4(nd, n0[g], buf, st4[g]);
-    }
+    if (live[g] && km.overlapped) load_input4(nd, n0[g], buf, st4[g]);
   }
 #pragma unroll
   for (int g = 0; g < G; ++g)
