@@ -10,6 +10,9 @@
   record formats, tuned after the first 100 steps.
 * 8x8 grid over the full 2 s of the batched sweep (20,000 steps, SWA, i16
   records) on the fused batch path, next to a 3x5 network, tuned after 2000 steps.
+* 24x24 AW network with the paper's 1 ms minimum delay (delays of 10..20 steps,
+  one delivery pass per 10 steps): 1500 steps, tuned on the two-kernel path
+  after 500.
 
 The oracle runs of all of them start together in spawned worker processes when
 the first test of this module asks for them, and compute while the GPU runs.
@@ -32,6 +35,7 @@ C2_STEPS, C2_ALONE, C2_CONCURRENT = 2400, 600, 900
 C3_STEPS, C3_TUNE_AT = 250, 100
 C4_STEPS, C4_TUNE_AT = 20_000, 2000
 COMPANION_STEPS = 7000
+MD_STEPS, MD_TUNE_AT = 1500, 500
 
 
 def _c2(regime):
@@ -48,6 +52,12 @@ def _c4():
 
 def _companion():
     return W.base_params(3, 5, 0.4, "AW", record_format=W.REC_F32), 1001
+
+
+def _md10():
+    p = dict(W.grid_24x24("AW")["params"])
+    p["min_delay"] = 10
+    return p, W.grid_24x24("AW")["seed"]
 
 
 @pytest.fixture(scope="module")
@@ -72,6 +82,7 @@ def oracle_runs(snn, oracle_mod):
         "c2_AW": (*_c2("AW"), C2_STEPS, 1, True),
         "c4": (*_c4(), C4_STEPS, 1, True),
         "companion": (*_companion(), COMPANION_STEPS, 1, True),
+        "md10": (*_md10(), MD_STEPS, 1, True),
     }
     ex = concurrent.futures.ProcessPoolExecutor(max_workers=len(jobs), mp_context=mp.get_context("spawn"))
     futs = {k: ex.submit(oracle_mod.simulate, *args) for k, args in jobs.items()}
@@ -131,3 +142,19 @@ def test_grid8x8_full_two_seconds_batched(snn, oracle_runs):
     assert_same(gpu_results(nets[1]), _oracle(oracle_runs, "companion"), COMPANION_STEPS, "3x5 AW f32")
     for g in nets:
         g.close()
+
+
+def test_grid24x24_one_ms_exchange_step(snn, oracle_runs):
+    """The paper's exchange step at the benchmarked size: delays of 10..20
+    steps, a delivery pass after every 10th step filling the next 10 inputs."""
+    p, seed = _md10()
+    g = snn.Network(p, seed)
+    g.run(MD_TUNE_AT)
+    g.autotune(50, path=0)
+    before = g.stats()["kernel_launches"]
+    g.run(MD_STEPS - MD_TUNE_AT)
+    launches = g.stats()["kernel_launches"] - before
+    # one update per step and one pass per 10 steps (window graphs count whole windows): ~1.1 per step
+    assert launches < 1.25 * (MD_STEPS - MD_TUNE_AT)
+    assert_same(gpu_results(g), _oracle(oracle_runs, "md10"), MD_STEPS, "24x24 AW min_delay 10")
+    g.close()
