@@ -218,7 +218,12 @@ int snn_set_launch(snn_handle h, const snn_launch *cfg);
 
 /* Time candidate launch shapes on this network for `trial_steps` steps each
  * and keep the fastest; the network's state, counters and records are
- * restored afterwards, so results are unchanged. */
+ * restored afterwards, so results are unchanged.  Stages: update shapes (and
+ * fused-path shapes), then delivery shapes for the best update shape, each
+ * stage timing every candidate once and its four fastest again (best of
+ * three); then the L2 window and the kernel overlap switched off only when
+ * that is at least 3% faster.  The result replaces the current shape only if
+ * at least 3% faster.  Synchronises the network's stream. */
 int snn_autotune(snn_handle h, uint32_t trial_steps);
 
 /* The same with the launch path fixed: path 0 tunes the two-kernel path only
