@@ -273,17 +273,16 @@ __device__ __forceinline__ void load_input4(const NetDev &nd, uint32_t n0, uint3
   g.I = ld_cg_i4(reinterpret_cast<const int4 *>(nd.acc + (size_t)buf * nd.N_pad) + (n0 >> 2));
 }
 
-// External drive of 4 neurons at step t up to the first event (Poisson counts
-// from one counter-based draw, word n mod 4 each; the first event's amplitude
-// from the table): adds it to I, the number of external events of the live
-// neurons to n_ext, and returns the counts (events 1..k-1 of a neuron with
-// k >= 2 are added by the caller).  Reads only the parameters and the table.
-__device__ __forceinline__ void drive4_first(const NetDev &nd, uint32_t n0, uint32_t t, int32_t (&I)[4],
-                                             uint32_t &n_ext, uint32_t (&kx)[4]) {
+// External drive of 4 neurons at step t (Poisson counts from one
+// counter-based draw, word n mod 4 each; amplitudes from the table): adds the
+// drive to I and the number of external events of the live neurons to n_ext.
+// Reads only the parameters and the amplitude table.
+__device__ __forceinline__ void drive4(const NetDev &nd, uint32_t n0, uint32_t t, int32_t (&I)[4], uint32_t &n_ext) {
   const uint4 R = philox4x32_10(n0 >> 2, t, 1u, 0u, nd.key0, nd.key1);
   const uint32_t Wv[4] = {R.x, R.y, R.z, R.w};
   uint32_t local = n0 % (uint32_t)kK;
   int pops[4];
+  uint32_t kx[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     pops[q] = pop_of_local(local);
@@ -293,86 +292,10 @@ __device__ __forceinline__ void drive4_first(const NetDev &nd, uint32_t n0, uint
 #pragma unroll
   for (int q = 0; q < 4; ++q)   // first external event: independent table loads
     if (kx[q]) I[q] += __ldg(nd.amp + pops[q] * kZTab + (Wv[q] & 0xFFFu));
+  extra_events_warp(nd, n0, t, kx, I);
 #pragma unroll
   for (int q = 0; q < 4; ++q)
     if (n0 + q < nd.N) n_ext += kx[q];
-}
-
-
-// Block-wide batch of extra external events (the update kernel): every warp
-// appends its neurons with k >= 2 to a shared list, the block's threads
-// compute one list entry each (one Philox draw per entry, so a block of 8
-// warps pays about one warp's draw instead of up to eight), and each neuron
-// adds its entry's sum.  A warp whose entries do not fit handles them itself.
-// Called by every thread of the block (three block barriers).
-constexpr uint32_t kExtraCap = 128;   // list entries per block: (n << 5) | k, k in 2..16
-struct ExtraList {
-  uint32_t n;
-  uint32_t ent[kExtraCap];
-  int32_t sum[kExtraCap];
-};
-
-template <int G>
-__device__ __forceinline__ void extra_events_block(const NetDev &nd, ExtraList &L, const uint32_t (&n0)[G],
-                                                   const bool (&live)[G], uint32_t t, const uint32_t (&kxp)[G],
-                                                   int32_t (&I)[G][4]) {
-  // kxp[g]: the 4 neurons' event counts, 8 bits each (0 for a group that is not live)
-  const uint32_t lane = lane_id(), lt = (1u << lane) - 1u;
-  if (threadIdx.x == 0) L.n = 0u;
-  __syncthreads();
-  uint32_t posp[G];     // list slot of each pending neuron, 8 bits each (0xFF: none)
-  uint32_t total = 0;
-#pragma unroll
-  for (int g = 0; g < G; ++g) {
-    posp[g] = 0xFFFFFFFFu;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const bool pend = ((kxp[g] >> (8 * q)) & 0xFFu) > 1u;
-      const uint32_t b = __ballot_sync(0xFFFFFFFFu, pend);
-      if (pend) posp[g] = (posp[g] & ~(0xFFu << (8 * q))) | (min(total + __popc(b & lt), 0xFEu) << (8 * q));
-      total += __popc(b);
-    }
-  }
-  uint32_t base = 0;
-  if (lane == 0 && total) base = atomicAdd(&L.n, total);
-  base = __shfl_sync(0xFFFFFFFFu, base, 0);
-  const bool fits = base + total <= kExtraCap;
-  if (total && !fits) {
-    // the warp's own entries: the slots below kExtraCap it reserved stay empty (k = 0)
-    for (uint32_t i = base + lane; i < kExtraCap; i += 32u) L.ent[i] = 0u;
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      const uint32_t k1[4] = {kxp[g] & 0xFFu, (kxp[g] >> 8) & 0xFFu, (kxp[g] >> 16) & 0xFFu, kxp[g] >> 24};
-      extra_events_warp(nd, n0[g], t, k1, I[g]);
-      posp[g] = 0xFFFFFFFFu;
-    }
-  } else if (total) {
-#pragma unroll
-    for (int g = 0; g < G; ++g)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const uint32_t ps = (posp[g] >> (8 * q)) & 0xFFu;
-        if (ps != 0xFFu) {
-          const uint32_t slot = base + ps;   // < kExtraCap: the warp's entries fit
-          posp[g] = (posp[g] & ~(0xFFu << (8 * q))) | (slot << (8 * q));
-          L.ent[slot] = ((n0[g] + (uint32_t)q) << 5) | ((kxp[g] >> (8 * q)) & 0xFFu);
-        }
-      }
-  }
-  __syncthreads();
-  const uint32_t used = min(L.n, kExtraCap);
-  for (uint32_t i = threadIdx.x; i < used; i += blockDim.x) {
-    const uint32_t e = L.ent[i], k = e & 31u, n = e >> 5;
-    L.sum[i] = k >= 2u ? extra_sum(nd, pop_of_local(n % (uint32_t)kK), k, n, t) : 0;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int g = 0; g < G; ++g)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint32_t ps = (posp[g] >> (8 * q)) & 0xFFu;
-      if (ps != 0xFFu) I[g][q] += L.sum[ps];
-    }
 }
 
 // Advance the 4 neurons of g by one step (Eq. 2) with total input I (the
@@ -402,6 +325,16 @@ __device__ __forceinline__ uint32_t integrate4(const NetDev &nd, uint32_t n0, ui
   return mask;
 }
 
+// One step of 4 neurons: the state and input loads are issued first and are
+// in flight while the drive is computed.
+__device__ __forceinline__ uint32_t update4(const NetDev &nd, uint32_t n0, uint32_t t, uint32_t buf, uint32_t &n_ext) {
+  Group4 g;
+  load_state4(nd, n0, g);
+  load_input4(nd, n0, buf, g);
+  int32_t I[4] = {0, 0, 0, 0};
+  drive4(nd, n0, t, I, n_ext);
+  return integrate4(nd, n0, buf, g, I);
+}
 
 // Slot (t mod D) of step t = t0 + k from the window's residue and the step's,
 // without a division.
@@ -883,24 +816,25 @@ __global__ void __launch_bounds__(kBuildWarpsMax * 32) k_build_rows(const __grid
 // it only after griddepcontrol.wait (the pass writes that buffer).  The trigger
 // that follows the wait lets the delivery pass after this step start on older
 // spikes.
-// The extra external events of the block are batched (extra_events_block).
 // One group per thread is capped at 48 registers (40 resident warps per SM), so
 // that a 720k-neuron grid (37 warps per SM) runs in a single wave.
 template <int BLOCK, int G>
 __global__ void __launch_bounds__(BLOCK, G == 1 ? 1280 / BLOCK : 1) k_update(const __grid_constant__ NetDev nd,
                                                                            uint32_t k, StepMod km) {
-  __shared__ ExtraList s_extra;
   uint32_t n0[G];
   bool live[G];
+  bool any = false;
 #pragma unroll
   for (int g = 0; g < G; ++g) {
     const uint32_t tile0 = ((blockIdx.x * G + g) * BLOCK + (threadIdx.x & ~31u)) * 4u;
     n0[g] = ((blockIdx.x * G + g) * BLOCK + threadIdx.x) * 4u;
     live[g] = tile0 < nd.N_pad;     // whole warps: N_pad is a multiple of 128
+    any |= live[g];
   }
+  if (!any) return;
   const NetWin w = *nd.win;   // written before the window's first kernel
   const uint32_t t = w.t0 + k;
-  if (t >= w.t_end) return;   // the same for the whole grid
+  if (t >= w.t_end) return;
   Group4 st4[G];
 #pragma unroll
   for (int g = 0; g < G; ++g)
@@ -909,19 +843,13 @@ __global__ void __launch_bounds__(BLOCK, G == 1 ? 1280 / BLOCK : 1) k_update(con
       if (!km.overlapped) load_input4(nd, n0[g], km.buf, st4[g]);
     }
   int32_t I[G][4];
-  uint32_t n_ext[G], kxp[G];
+  uint32_t n_ext[G];
 #pragma unroll
   for (int g = 0; g < G; ++g) {
     I[g][0] = I[g][1] = I[g][2] = I[g][3] = 0;
     n_ext[g] = 0;
-    kxp[g] = 0;
-    if (live[g]) {
-      uint32_t kx[4];
-      drive4_first(nd, n0[g], t, I[g], n_ext[g], kx);
-      kxp[g] = kx[0] | (kx[1] << 8) | (kx[2] << 16) | (kx[3] << 24);   // each count <= 16
-    }
+    if (live[g]) drive4(nd, n0[g], t, I[g], n_ext[g]);
   }
-  extra_events_block<G>(nd, s_extra, n0, live, t, kxp, I);   // every thread of the block, live or not
   pdl_wait();      // the previous kernel (and everything before it) is complete
   pdl_trigger();
   const uint32_t slot = step_slot(nd, w, km), buf = km.buf;
@@ -1020,7 +948,6 @@ __global__ void __launch_bounds__(512) k_fused(const __grid_constant__ FusedTabl
   extern __shared__ __align__(128) uint8_t smem[];   // the item's spike ids (4 * blockDim)
   __shared__ NetDev nd;
   __shared__ NetWin s_win;
-  __shared__ ExtraList s_extra;
   __shared__ uint32_t s_count;
   __shared__ uint32_t s_net;
   uint32_t *s_ids = reinterpret_cast<uint32_t *>(smem);
@@ -1050,24 +977,11 @@ __global__ void __launch_bounds__(512) k_fused(const __grid_constant__ FusedTabl
     const uint32_t n0 = item.n_begin + threadIdx.x * 4u;
     const uint32_t warp_first = item.n_begin + warp * 128u;
     const uint32_t tm = t % nd.D, tb = t % nd.nbuf;
-    {
-      const bool live1[1] = {warp_first < nd.N_pad};
+    if (warp_first < nd.N_pad) {
+      uint32_t n_ext[1] = {0};
+      const uint32_t mask[1] = {update4(nd, n0, t, tb, n_ext[0])};
       const uint32_t a1[1] = {n0};
-      Group4 g4;
-      int32_t I1[1][4] = {{0, 0, 0, 0}};
-      uint32_t n_ext[1] = {0}, kxp[1] = {0};
-      if (live1[0]) {
-        load_state4(nd, n0, g4);
-        load_input4(nd, n0, tb, g4);
-        uint32_t kx[4];
-        drive4_first(nd, n0, t, I1[0], n_ext[0], kx);
-        kxp[0] = kx[0] | (kx[1] << 8) | (kx[2] << 16) | (kx[3] << 24);
-      }
-      extra_events_block<1>(nd, s_extra, a1, live1, t, kxp, I1);   // every thread of the block
-      if (live1[0]) {
-        const uint32_t mask[1] = {integrate4(nd, n0, tb, g4, I1[0])};
-        record_warp<1>(nd, mask, a1, n_ext, t, tm, k, s_win.bin0, s_ids, &s_count);
-      }
+      record_warp<1>(nd, mask, a1, n_ext, t, tm, k, s_win.bin0, s_ids, &s_count);
     }
     __syncthreads();
     if ((t + 1u) % nd.kmin == 0u) {   // the last step of an exchange period: delivery pass
@@ -1121,25 +1035,7 @@ static size_t build_smem_budget() {
   return b;
 }
 
-// The update kernel's blocks hold ~1 KB of shared memory (the extra-event
-// list) and the delivery kernel's none.  Both ask for the same small
-// shared-memory carveout, so that an SM running blocks of one never has to
-// drain before it can take blocks of the other (the kernels overlap).
-constexpr int kStepCarveoutPercent = 8;
-
 cudaError_t prepare_kernels() {
-  cudaError_t e = cudaSuccess;
-  auto carve = [&](const void *f) {
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, kStepCarveoutPercent);
-  };
-  carve(reinterpret_cast<const void *>(k_deliver<1>));
-  carve(reinterpret_cast<const void *>(k_deliver<kMaxPreChunks>));
-#define SNN_CARVE(B, G) carve(reinterpret_cast<const void *>(k_update<B, G>));
-  SNN_CARVE(64, 1) SNN_CARVE(128, 1) SNN_CARVE(128, 2) SNN_CARVE(128, 4)
-  SNN_CARVE(256, 1) SNN_CARVE(256, 2) SNN_CARVE(256, 4) SNN_CARVE(512, 1) SNN_CARVE(512, 2)
-#undef SNN_CARVE
-  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_build_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)build_smem_budget());
 }
 
