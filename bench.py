@@ -365,10 +365,10 @@ def run_gb300(args, dist: Dist):
         nets.append(snn.Network(wl["params"], wl["seed"] + 7919 * dist.rank, stream=streams[-1].cuda_stream))
         names.append(reg)
     # Two ways to advance the pair: "concurrent" (two-kernel path, each network
-    # tuned alone, each on its own stream) and "batch" (both networks in one
-    # fused kernel per step, shape tuned on the pair).  After the initial
-    # volley both are tuned and timed on alternating stretches of the same run;
-    # the faster one is benchmarked.
+    # tuned alone, then the pair tuned running together, each on its own
+    # stream) and "batch" (both networks in one fused kernel per step, shape
+    # tuned on the pair).  After the initial volley both are tuned and timed on
+    # alternating stretches of the same run; the faster one is benchmarked.
     form, form_trial = ("sequential" if args.sequential else "concurrent"), None
     if not args.no_tune:
         for n in nets:
@@ -377,6 +377,7 @@ def run_gb300(args, dist: Dist):
         cfg_conc = [n.launch for n in nets]
         cfg_batch = None
         if not args.sequential:
+            cfg_conc = snn.autotune_concurrent(nets, 400)
             cfg_batch = snn.autotune_batch(nets, 200)
             form_trial = {"concurrent_ms": 0.0, "batch_ms": 0.0, "steps_each": 3 * 700}
             for _ in range(3):
@@ -609,7 +610,8 @@ def run_gb300(args, dist: Dist):
                        "launch": launch_cfgs, "parallelism": f"replicas x{dist.world}",
                        "networks_run": {"sequential": "one after the other",
                                         "concurrent": "concurrently, one CUDA stream each, two-kernel path "
-                                                      "(snn_run_concurrent)",
+                                                      "(snn_run_concurrent), shapes tuned with both running "
+                                                      "(snn_autotune_concurrent)",
                                         "batch": "together, one fused kernel per step for both networks "
                                                  "(snn_run_batch)"}[form],
                        "form_trial": form_trial},

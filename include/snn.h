@@ -242,6 +242,18 @@ int snn_autotune_path(snn_handle h, uint32_t trial_steps, int32_t path);
  * spike history. */
 int snn_autotune_batch(const snn_handle *hs, int32_t n, uint32_t trial_steps);
 
+/* The same for networks advanced together by snn_run_concurrent (launch path
+ * 0 on every network): candidate update and delivery shapes, one shape for
+ * all networks, are timed running concurrently on the networks' own streams
+ * for `trial_steps` steps each (every candidate once, the four fastest again,
+ * best of three), from snapshots of every network (state, counters and
+ * records restored afterwards, so results are unchanged).  The fastest
+ * replaces the networks' current shapes only if at least 3% faster than them
+ * running together.  Shapes that are best for a network alone can be slower
+ * when networks share the GPU (two 24x24 networks: ~4%).  At most 1024
+ * networks; synchronises their streams.  The paper has no counterpart. */
+int snn_autotune_concurrent(const snn_handle *hs, int32_t n, uint32_t trial_steps);
+
 /* Measure the two-kernel path on the next `steps` (1..window) steps, then
  * advance the network by them.  The steps run twice from the same state on the
  * network's stream: once captured into one CUDA graph as snn_run runs them

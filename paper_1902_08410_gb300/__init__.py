@@ -247,6 +247,15 @@ def autotune_batch(nets, trial_steps: int = 200) -> dict:
     return nets[0].launch
 
 
+def autotune_concurrent(nets, trial_steps: int = 200) -> list:
+    """Choose two-kernel shapes for networks run together by run_concurrent
+    (see snn_autotune_concurrent); returns every network's shape."""
+    nets = list(nets)
+    hs = (ctypes.c_void_p * len(nets))(*[n.handle.value for n in nets])
+    _check(lib().snn_autotune_concurrent(hs, len(nets), int(trial_steps)))
+    return [n.launch for n in nets]
+
+
 def run_batch(nets, steps) -> None:
     """Advance several networks together with one fused kernel per time step."""
     nets = list(nets)

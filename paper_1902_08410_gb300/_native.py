@@ -107,7 +107,7 @@ EXPORTS = ["snn_set_allocator", "snn_footprint", "snn_build_network", "snn_run",
            "snn_read_spikes", "snn_rates", "snn_read_state", "snn_read_row", "snn_get_stats",
            "snn_get_launch", "snn_set_launch", "snn_autotune", "snn_autotune_path", "snn_free", "snn_last_error",
            "snn_time_kernels", "snn_build_rows_static", "snn_run_concurrent",
-           "snn_autotune_batch"]
+           "snn_autotune_batch", "snn_autotune_concurrent"]
 
 _lib = None
 
@@ -141,6 +141,7 @@ def load(build_if_needed: bool = True):
         "snn_autotune": ([vp, u32], ctypes.c_int),
         "snn_autotune_path": ([vp, u32, i32], ctypes.c_int),
         "snn_autotune_batch": ([P(vp), i32, u32], ctypes.c_int),
+        "snn_autotune_concurrent": ([P(vp), i32, u32], ctypes.c_int),
         "snn_free": ([vp], None),
         "snn_last_error": ([], ctypes.c_char_p),
         "snn_time_kernels": ([vp, u32, P(ctypes.c_double)], ctypes.c_int),

@@ -1395,16 +1395,11 @@ extern "C" int snn_time_kernels(snn_handle h, uint32_t steps, double *ms_out) {
 // batch tuner: fused-kernel shapes timed on the whole batch from snapshots of
 // every network, restored after each trial
 // ---------------------------------------------------------------------------
-extern "C" int snn_autotune_batch(const snn_handle *hs, int32_t n, uint32_t trial_steps) {
-  if (!hs || n < 1) return fail(SNN_ERR_ARG, "empty batch");
-  if (n > 65535) return fail(SNN_ERR_LIMIT, "more than 65535 networks in one batch");
-  if (trial_steps == 0) return fail(SNN_ERR_ARG, "trial_steps must be > 0");
-  for (int i = 0; i < n; ++i) {
-    if (!hs[i]) return fail(SNN_ERR_ARG, "null handle in batch");
-    if (hs[i]->broken) return fail(SNN_ERR_STATE, "network is invalid after an earlier failure");
-    for (int j = 0; j < i; ++j)
-      if (hs[j] == hs[i]) return fail(SNN_ERR_ARG, "a network appears twice in the batch");
-  }
+// Snapshots of several networks for the multi-network tuners: state (V, c,
+// ref, input buffers, spike history), counters, records and launch shape,
+// restored after every trial so that the networks' results are unchanged.
+// Copies are ordered on the first network's stream; the others wait for it.
+struct MultiSnapshot {
   struct Saved {
     DevBuf snap;
     uint64_t t, spikes, ext;
@@ -1412,32 +1407,37 @@ extern "C" int snn_autotune_batch(const snn_handle *hs, int32_t n, uint32_t tria
     std::vector<uint32_t> rates;
     snn_launch cfg;
   };
-  std::vector<Saved> sv((size_t)n);
-  cudaStream_t s = hs[0]->stream;
-  for (int i = 0; i < n; ++i)
-    if (hs[i]->stream != s) CU_TRY(cudaStreamSynchronize(hs[i]->stream));
-  struct G {
-    std::vector<Saved> *v;
-    cudaStream_t s;
-    ~G() {
-      cudaStreamSynchronize(s);
-      for (auto &x : *v) x.snap.release();
-    }
-  } guard{&sv, s};
-  for (int i = 0; i < n; ++i) {
-    snn_net *h = hs[i];
-    int rc = dev_alloc(sv[i].snap, h->L.off_rows);   // V, c, ref, input buffers, spike history
-    if (rc) return rc;
-    CU_TRY(cudaMemcpyAsync(sv[i].snap.p, h->arena.p, h->L.off_rows, cudaMemcpyDeviceToDevice, s));
-    sv[i].t = h->t;
-    sv[i].spikes = h->spikes;
-    sv[i].ext = h->ext_events;
-    sv[i].raster = h->raster.size();
-    sv[i].sorted = h->raster_sorted;
-    sv[i].rates = h->rates;
-    sv[i].cfg = h->cfg;
+  const snn_handle *hs = nullptr;
+  int n = 0;
+  cudaStream_t s = nullptr;
+  std::vector<Saved> sv;
+  ~MultiSnapshot() {
+    if (s) cudaStreamSynchronize(s);
+    for (auto &x : sv) x.snap.release();
   }
-  auto restore = [&]() -> int {
+  int take(const snn_handle *hs_, int n_) {
+    hs = hs_;
+    n = n_;
+    s = hs[0]->stream;
+    for (int i = 0; i < n; ++i)
+      if (hs[i]->stream != s) CU_TRY(cudaStreamSynchronize(hs[i]->stream));
+    sv.resize((size_t)n);
+    for (int i = 0; i < n; ++i) {
+      snn_net *h = hs[i];
+      int rc = dev_alloc(sv[i].snap, h->L.off_rows);   // V, c, ref, input buffers, spike history
+      if (rc) return rc;
+      CU_TRY(cudaMemcpyAsync(sv[i].snap.p, h->arena.p, h->L.off_rows, cudaMemcpyDeviceToDevice, s));
+      sv[i].t = h->t;
+      sv[i].spikes = h->spikes;
+      sv[i].ext = h->ext_events;
+      sv[i].raster = h->raster.size();
+      sv[i].sorted = h->raster_sorted;
+      sv[i].rates = h->rates;
+      sv[i].cfg = h->cfg;
+    }
+    return SNN_OK;
+  }
+  int restore() {
     for (int i = 0; i < n; ++i) {
       snn_net *h = hs[i];
       uint8_t *base = static_cast<uint8_t *>(h->arena.p);
@@ -1450,8 +1450,31 @@ extern "C" int snn_autotune_batch(const snn_handle *hs, int32_t n, uint32_t tria
       h->raster_sorted = std::min(sv[i].sorted, sv[i].raster);
       h->rates = sv[i].rates;
     }
+    CU_TRY(cudaStreamSynchronize(s));   // every network's stream may use its state next
     return SNN_OK;
-  };
+  }
+};
+
+static int check_multi(const snn_handle *hs, int32_t n, uint32_t trial_steps, int32_t max_n) {
+  if (!hs || n < 1) return fail(SNN_ERR_ARG, "no networks");
+  if (n > max_n) return fail(SNN_ERR_LIMIT, "too many networks in one call");
+  if (trial_steps == 0) return fail(SNN_ERR_ARG, "trial_steps must be > 0");
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i]) return fail(SNN_ERR_ARG, "null handle");
+    if (hs[i]->broken) return fail(SNN_ERR_STATE, "network is invalid after an earlier failure");
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return fail(SNN_ERR_ARG, "a network appears twice");
+  }
+  return SNN_OK;
+}
+
+extern "C" int snn_autotune_batch(const snn_handle *hs, int32_t n, uint32_t trial_steps) {
+  int rc = check_multi(hs, n, trial_steps, 65535);
+  if (rc) return rc;
+  MultiSnapshot snap;
+  rc = snap.take(hs, n);
+  if (rc) return rc;
+  cudaStream_t s = snap.s;
   cudaEvent_t e0, e1;
   CU_TRY(cudaEventCreate(&e0));
   CU_TRY(cudaEventCreate(&e1));
@@ -1462,7 +1485,7 @@ extern "C" int snn_autotune_batch(const snn_handle *hs, int32_t n, uint32_t tria
     for (int i = 0; i < n; ++i) hs[i]->cfg = c;
     *ms_out = 1e30f;
     for (int rep = 0; rep <= reps; ++rep) {
-      int r = restore();
+      int r = snap.restore();
       if (r) return r;
       CU_TRY(cudaEventRecord(e0, s));
       r = run_fused(hs, steps.data(), n);
@@ -1497,10 +1520,97 @@ extern "C" int snn_autotune_batch(const snn_handle *hs, int32_t n, uint32_t tria
       }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  int rr = restore();
-  CU_TRY(cudaStreamSynchronize(s));
+  int rr = snap.restore();
   const bool replace = status == SNN_OK && best_ms < 0.97f * orig_ms;   // the incumbent unless clearly slower
-  for (int i = 0; i < n; ++i) hs[i]->cfg = (status == SNN_OK) ? (replace ? best : orig) : sv[i].cfg;
+  for (int i = 0; i < n; ++i) hs[i]->cfg = (status == SNN_OK) ? (replace ? best : orig) : snap.sv[i].cfg;
+  return status != SNN_OK ? status : rr;
+}
+
+extern "C" int snn_autotune_concurrent(const snn_handle *hs, int32_t n, uint32_t trial_steps) {
+  int rc = check_multi(hs, n, trial_steps, 1024);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i)
+    if (hs[i]->cfg.path != 0) return fail(SNN_ERR_ARG, "snn_autotune_concurrent tunes the two-kernel path (launch path 0)");
+  MultiSnapshot snap;
+  rc = snap.take(hs, n);
+  if (rc) return rc;
+  // events: the start on the first stream (the others wait for it), the end on every stream
+  std::vector<cudaEvent_t> ev((size_t)n + 1, nullptr);
+  struct EvGuard {
+    std::vector<cudaEvent_t> *v;
+    ~EvGuard() {
+      for (auto e : *v)
+        if (e) cudaEventDestroy(e);
+    }
+  } eg{&ev};
+  for (auto &e : ev) CU_TRY(cudaEventCreate(&e));
+  std::vector<uint64_t> steps((size_t)n, trial_steps);
+  // one assignment of shapes (per network) run concurrently: the first pass
+  // captures the graphs, the time is the best of the next `reps` passes
+  auto trial = [&](const std::vector<snn_launch> &cs, int reps, float *ms_out) -> int {
+    for (int i = 0; i < n; ++i) hs[i]->cfg = cs[(size_t)i];
+    *ms_out = 1e30f;
+    for (int rep = 0; rep <= reps; ++rep) {
+      int r = snap.restore();
+      if (r) return r;
+      CU_TRY(cudaEventRecord(ev[0], hs[0]->stream));
+      for (int i = 1; i < n; ++i) CU_TRY(cudaStreamWaitEvent(hs[i]->stream, ev[0], 0));
+      r = run_plain_many(hs, steps.data(), n);
+      if (r) return r;
+      for (int i = 0; i < n; ++i) CU_TRY(cudaEventRecord(ev[(size_t)i + 1], hs[i]->stream));
+      float ms = 0;
+      for (int i = 0; i < n; ++i) {
+        CU_TRY(cudaEventSynchronize(ev[(size_t)i + 1]));
+        float x = 0;
+        CU_TRY(cudaEventElapsedTime(&x, ev[0], ev[(size_t)i + 1]));
+        ms = std::max(ms, x);
+      }
+      if (rep > 0) *ms_out = std::min(*ms_out, ms);
+    }
+    return SNN_OK;
+  };
+  std::vector<snn_launch> orig((size_t)n);
+  for (int i = 0; i < n; ++i) orig[(size_t)i] = hs[i]->cfg;
+  float orig_ms = 1e30f;
+  int status = trial(orig, 3, &orig_ms);
+  // candidates: one update and delivery shape for every network (the
+  // networks' other settings kept); all timed once, the four fastest again
+  std::vector<std::vector<snn_launch>> cands;
+  const int dwb[][2] = {{16, 3}, {16, 2}, {8, 4}, {8, 3}, {8, 6}, {4, 8}};
+  for (int ub : {128, 256})
+    for (const auto &w : dwb)
+      for (int ln : {16, 32}) {
+        std::vector<snn_launch> cs = orig;
+        for (auto &c : cs) {
+          c.update_block = ub;
+          c.update_groups = 1;
+          c.deliver_warps = w[0];
+          c.deliver_blocks = w[1];
+          c.deliver_lanes = ln;
+        }
+        cands.push_back(cs);
+      }
+  std::vector<std::pair<float, size_t>> timed;
+  for (size_t i = 0; i < cands.size() && status == SNN_OK; ++i) {
+    float ms = 0;
+    status = trial(cands[i], 1, &ms);
+    timed.emplace_back(ms, i);
+  }
+  std::sort(timed.begin(), timed.end());
+  float best_ms = 1e30f;
+  size_t best = 0;
+  for (size_t r = 0; r < timed.size() && r < 4 && status == SNN_OK; ++r) {
+    float ms = 0;
+    status = trial(cands[timed[r].second], 3, &ms);
+    if (status == SNN_OK && ms < best_ms) {
+      best_ms = ms;
+      best = timed[r].second;
+    }
+  }
+  int rr = snap.restore();
+  const bool replace = status == SNN_OK && best_ms < 0.97f * orig_ms;   // the incumbents unless clearly slower
+  for (int i = 0; i < n; ++i)
+    hs[i]->cfg = (status == SNN_OK) ? (replace ? cands[best][(size_t)i] : orig[(size_t)i]) : snap.sv[(size_t)i].cfg;
   return status != SNN_OK ? status : rr;
 }
 

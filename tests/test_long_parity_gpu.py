@@ -3,9 +3,10 @@
 * 24x24 grid (720k neurons, 0.81G synapses, lambda 1.0, f32 records), the SWA and
   the AW network: 2400 steps each, advanced in both ways the benchmark can
   advance them (the default launch shape alone first, then the two-kernel
-  shape the tuner picks with both networks concurrently on their own streams
-  through snn_run_concurrent, then both in one fused kernel per step with the
-  shape the batch tuner picks, through snn_run_batch).
+  shapes the tuners pick, each network alone and then both together, with
+  both networks concurrently on their own streams through snn_run_concurrent,
+  then both in one fused kernel per step with the shape the batch tuner picks,
+  through snn_run_batch).
 * 64x64 grid (5.12M neurons, 5.76G synapses, AW, lambda 1.0): 250 steps on both
   record formats, tuned after the first 100 steps.
 * 8x8 grid over the full 2 s of the batched sweep (20,000 steps, SWA, i16
@@ -109,6 +110,7 @@ def test_grid24x24_swa_aw_as_benchmarked(snn, oracle_runs):
     for g in nets:
         g.run(C2_ALONE)
         g.autotune(50, path=0)
+    snn.autotune_concurrent(nets, 50)
     snn.run_concurrent(nets, C2_CONCURRENT)
     cfg = snn.autotune_batch(nets, 50)
     assert cfg["path"] == 1

@@ -257,6 +257,8 @@ def test_run_concurrent_matches_oracle(snn, oracle_mod):
         nets.append(g)
     first = [c[3] // 3 for c in cases]
     snn.run_concurrent(nets, first)
+    shapes = snn.autotune_concurrent(nets, 30)   # the pair tuner restores every network
+    assert all(sh["path"] == 0 for sh in shapes)
     snn.run_concurrent(nets, [c[3] - f for c, f in zip(cases, first)])
     for g, (p, seed, _, steps, _) in zip(nets, cases):
         _assert_same_run(g, _oracle(oracle_mod, p, seed, steps), steps)
@@ -265,6 +267,9 @@ def test_run_concurrent_matches_oracle(snn, oracle_mod):
     g.launch = {"path": 1}
     with pytest.raises(snn.SnnError):
         snn.run_concurrent([g], [10])
+    with pytest.raises(snn.SnnError):
+        snn.autotune_concurrent([g], 10)
+    g.close()
 
 
 # ---------------------------------------------------------------------------
