@@ -546,9 +546,7 @@ __device__ __forceinline__ void deliver_segments(const NetDev &nd, const WarpPre
     if (d == 0) continue;   // g past the total (last round)
     const uint32_t s = ld_cg_u32(nd.hist + (size_t)slot_back(Tm, d, D) * nd.N_pad + (g - below));
     const uint16_t *o = nd.offs + (size_t)s * nd.os;
-    const uint32_t a = o[d - 1u], b = o[d];
-    if (sub == 0) prefetch_next_group(nd, s, o, d, b);   // read at a later pass
-    add_records(nd, acc_T, s, a, b, sub, lanes);
+    add_records(nd, acc_T, s, o[d - 1u], o[d], sub, lanes);
   }
 }
 
