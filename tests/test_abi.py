@@ -51,6 +51,18 @@ def test_footprint_host_only(snn):
     assert snn.footprint(p16) < b
 
 
+def test_footprint_follows_min_delay(snn):
+    """2 max(1, min_delay) input buffers and a history of n_delay + max(1, min_delay)
+    step slots, int32 per padded neuron each (include/snn.h, snn_footprint)."""
+    p1 = W.base_params(2, 2, 1.0)
+    p10 = dict(p1, min_delay=10)
+    n_pad = 5120                                   # 5000 neurons rounded up to 128
+    extra_buffers = (2 * 10 - 2 * 1) * n_pad * 4
+    extra_history = ((20 + 10) - (20 + 1)) * n_pad * 4
+    assert snn.footprint(p10) - snn.footprint(p1) == extra_buffers + extra_history
+    assert snn.footprint(dict(p1, min_delay=0)) == snn.footprint(p1)   # 0 is read as 1
+
+
 @pytest.mark.parametrize("field,value,code", [
     ("gx", 0, -1), ("lambda", 0.0, -1), ("n_delay", 0, -1), ("n_delay", 300, -1),
     ("record_format", 7, -1), ("out_degree", 5000, -6), ("gx", 120, -6), ("bin_steps", 0, -1),
